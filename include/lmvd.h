@@ -1,0 +1,147 @@
+/* lmvd: one Runge-Kutta substage of the low-Mach, variable-density pseudospectral method of
+ * Reuter, Oliver and Moser (arXiv:2206.09878) on one GB300 GPU.
+ *
+ * The state S = (z, Omega2, m2^d, <m1>, <m3>) of Sec. 4.4 (Eq. DNS_system) is advanced by
+ * Algorithm 2: m^d from Eq. phi_poisson / md_recon, R_z and the BDF-like guess of
+ * Eq. dzdt_guesses, k_f fixed-point applications of L (Eq. y_k, Sec. 4.3), m^c from
+ * Eq. COM_fourier / CF_fourier / mc_recon / mc_mean, the right-hand sides of Eq. DNS_system,
+ * and the segregated midpoint RK2 update (Sec. 3.3).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Spectral arrays are complex128 (interleaved re, im), C-contiguous, layout [y][kz][kx]:
+ *   y  : B-spline coefficient index, ny rows (ny + 1 for m2, whose space has one more function);
+ *   kz : nz slots in FFT order (slot j is kz = j for j < nz/2, j - nz for j > nz/2);
+ *   kx : nx/2 + 1 slots, kx = 0 .. nx/2.
+ * Retained modes are |kx| < nx/2, |kz| < nz/2 (Eq. disc_f); the Nyquist slots kx = nx/2 and
+ * kz = nz/2 must be zero. The kx = 0 column is Hermitian in kz (f(0,-kz) = conj f(0,kz)).
+ * The plane means <m1>, <m3> are float64 vectors of ny B-spline coefficients.
+ * y-basis: clamped B-splines on uniform breakpoints of [y0, y1] (Appendix C), order p for all
+ * fields but m2 and order p + 1 for m2, collocated at Greville abscissae.
+ * Walls at y0 and y1 are no-slip; dz/dy = 0 there.
+ *
+ * Pointers passed to set/get calls may be device memory or host memory (pinned host memory
+ * gives asynchronous copies); they are read or written on the context's stream with
+ * cudaMemcpyDefault and remain owned by the caller. The library owns only its own workspace.
+ * Every call is asynchronous on the context's stream unless it says otherwise; a caller that
+ * reads an output must synchronize that stream (or call lmvd_synchronize).
+ *
+ * Errors: every int-returning call returns LMVD_OK (0) or a negative LMVD_ERR_* code and never
+ * traps the GPU. The first error is also latched in the context (lmvd_status).
+ */
+#ifndef LMVD_H
+#define LMVD_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LMVD_OK 0
+#define LMVD_ERR_INVALID_ARG (-1)
+#define LMVD_ERR_CUDA (-2)
+#define LMVD_ERR_OOM (-3)
+#define LMVD_ERR_NONFINITE (-4)
+#define LMVD_ERR_UNSUPPORTED (-5)
+
+/* Problem definition, copied at lmvd_create (all host values).
+ * nx, nz      : Fourier grid (even; 3*nx/2 and 3*nz/2 must have no prime factors other than 2, 3).
+ * ny          : number of order-p B-splines in y (>= p + 4).
+ * spline_order: p (4 .. 8).
+ * lx, lz      : periods in x and z;  y0 < y1: wall positions.
+ * re, sc, fr  : Reynolds, Schmidt, Froude numbers: mu = 1/re, rho D_z = 1/(re sc), g = 1/fr^2 along -y.
+ * rho_heavy, rho_light: densities of the pure fluids; EOS rho = rl rh / (rh - (rh - rl) z) (Sec. 5).
+ * dt          : time step of one RK2 step (two substages).
+ * kf          : fixed-point applications of L per substage (Sec. 3.2).
+ * beta_n, beta_p: free parameters of the guesses of Eq. dzdt_guesses (paper: 0 and -4).
+ * n_startup   : fixed-point iterations from dz/dt = 0 used by lmvd_set_state without history.
+ */
+typedef struct {
+  int nx, ny, nz, spline_order;
+  double lx, lz, y0, y1;
+  double re, sc, fr, rho_heavy, rho_light;
+  double dt;
+  int kf;
+  double beta_n, beta_p;
+  int n_startup;
+} lmvd_config;
+
+typedef struct lmvd_ctx lmvd_ctx;
+
+/* Fill *cfg with the defaults (p = 6, 2 pi periods, walls at -1 and +1, Re = 1000, Sc = Fr = 1,
+ * density ratio 3, dt = 1e-3, kf = 4, beta_n = 0, beta_p = -4, n_startup = 20) for the given grid.
+ * Returns LMVD_ERR_INVALID_ARG if cfg is NULL. */
+int lmvd_default_config(lmvd_config* cfg, int nx, int ny, int nz);
+
+/* Build the y-operators (Appendix C), factor the per-mode m^c and m2^d systems (Sec. 4.1-4.2),
+ * plan the transforms and allocate all device workspace (one allocation) on the current device.
+ * cuda_stream: a cudaStream_t (NULL = legacy default stream) on which every later call runs.
+ * *out receives a context owned by the caller until lmvd_destroy. Synchronous.
+ * Errors: INVALID_ARG (NULL pointers, bad sizes), UNSUPPORTED (grid sizes the transforms do not
+ * handle), OOM (device allocation failed), CUDA (any other CUDA failure). */
+int lmvd_create(const lmvd_config* cfg, void* cuda_stream, lmvd_ctx** out);
+
+/* Release all device memory of the context. NULL is ignored. */
+void lmvd_destroy(lmvd_ctx* ctx);
+
+/* Load the state (Sec. 4.4: z, Omega2, m2^d -- held instead of phi2 = (d2/dy2 - k^2) m2^d -- and
+ * the plane means). z_hat, omega2_hat: ny rows; m2d_hat: ny + 1 rows; mean_m1, mean_m3: ny doubles.
+ * history: NULL, or a blob of lmvd_history_bytes() bytes from lmvd_get_state (restart).
+ * With history == NULL the substage counter is reset to 0 and a start-up runs: n_startup
+ * applications of the fixed point of Eq. dz_fixedpoint_stageone from dz/dt = 0, then the z history
+ * of Eq. dzdt_guesses is back-filled with Taylor steps z - j dt/2 dz/dt, j = 1, 2, 3 (the paper
+ * leaves start-up open). Nyquist slots and the k = 0 slot of Omega2 and m2^d are zeroed.
+ * Errors: INVALID_ARG (NULL ctx or state pointer), CUDA. */
+int lmvd_set_state(lmvd_ctx* ctx, const void* z_hat, const void* omega2_hat, const void* m2d_hat,
+                   const double* mean_m1, const double* mean_m3, const void* history);
+
+/* Copy the state out (same layouts as lmvd_set_state). Any pointer may be NULL to skip it.
+ * history, if not NULL, receives lmvd_history_bytes() bytes: int64 substage counter, 8 bytes
+ * padding, then z^{s-1}, z^{s-2}, z^{s-3}, (dz/dt)^{s-1}, RHS_Omega2^{s-1} (ny rows),
+ * RHS_phi2^{s-1} (ny + 1 rows) as spectral arrays, then RHS_<m1>^{s-1}, RHS_<m3>^{s-1} (ny doubles
+ * each). The RHS arrays hold values at collocation points. Asynchronous. Errors: INVALID_ARG, CUDA. */
+int lmvd_get_state(lmvd_ctx* ctx, void* z_hat, void* omega2_hat, void* m2d_hat, double* mean_m1,
+                   double* mean_m3, void* history);
+
+/* Bytes of the history blob. 0 if ctx is NULL. */
+size_t lmvd_history_bytes(const lmvd_ctx* ctx);
+
+/* One substage s -> s + 1 of Algorithm 2 (steps 1-6): stage n for even s, stage ' (t_{n+1/2})
+ * for odd s. Asynchronous; enqueues kernels only. Errors: INVALID_ARG, CUDA. */
+int lmvd_advance_substage(lmvd_ctx* ctx);
+
+/* nsteps RK2 steps = 2 * nsteps substages. Errors as lmvd_advance_substage. */
+int lmvd_step(lmvd_ctx* ctx, int nsteps);
+
+/* Intermediate fields of the last substage, for testing and diagnostics (B coefficients unless
+ * stated): which = LMVD_FIELD_*. out: caller-owned host or device buffer of lmvd_field_bytes().
+ * Errors: INVALID_ARG (unknown field, NULL), CUDA. */
+#define LMVD_FIELD_RZ 0        /* R_z (Sec. 2.1)                                  ny rows   */
+#define LMVD_FIELD_ZDOT 1      /* (dz/dt)^{s,k_f}                                 ny rows   */
+#define LMVD_FIELD_RHO_T 2     /* f'(z) (dz/dt)^{s,k_f}                           ny rows   */
+#define LMVD_FIELD_MC1 3       /* m1^c                                            ny rows   */
+#define LMVD_FIELD_MC2 4       /* m2^c (order p + 1 space)                        ny+1 rows */
+#define LMVD_FIELD_MC3 5       /* m3^c                                            ny rows   */
+#define LMVD_FIELD_R_OMEGA2 6  /* RHS_Omega2 at the order-p Greville points       ny rows   */
+#define LMVD_FIELD_R_PHI2 7    /* RHS_phi2 at the order-(p+1) Greville points     ny+1 rows */
+#define LMVD_FIELD_R_MEANS 8   /* RHS_<m1>, RHS_<m3> at the Greville points: 2*ny doubles   */
+int lmvd_get_field(lmvd_ctx* ctx, int which, void* out);
+size_t lmvd_field_bytes(const lmvd_ctx* ctx, int which);
+
+/* Substage counter s (0 after a start-up). -1 if ctx is NULL. */
+int lmvd_substage_index(const lmvd_ctx* ctx);
+
+/* Block until all work of the context's stream is done; returns the latched status or CUDA. */
+int lmvd_synchronize(lmvd_ctx* ctx);
+
+/* First error latched in the context (LMVD_OK if none). */
+int lmvd_status(const lmvd_ctx* ctx);
+
+/* Static description of an error code. */
+const char* lmvd_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

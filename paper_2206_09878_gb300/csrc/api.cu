@@ -1,0 +1,640 @@
+// C-ABI of liblmvd (include/lmvd.h) and the host orchestration of one substage (Algorithm 2).
+// The host only enqueues kernels on the context's stream; no call synchronises except
+// lmvd_create, lmvd_synchronize and lmvd_set_state when it must read a history counter.
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <stdexcept>
+
+#include "basis.h"
+#include "ykernels.h"
+
+using namespace lmvd;
+
+struct lmvd_ctx {
+  Ctx c;
+  long long s_blob = 0;
+};
+
+namespace {
+
+constexpr int TPB_MODE = 128;
+
+unsigned mode_blocks(const Grid& g) { return (unsigned)((g.M + TPB_MODE - 1) / TPB_MODE); }
+unsigned elem_blocks(size_t n) {
+  size_t b = (n + 255) / 256;
+  return (unsigned)std::min<size_t>(b, 152 * 32);
+}
+
+int latch(Ctx& c, int err) {
+  if (err != LMVD_OK && c.status == LMVD_OK) c.status = err;
+  return err;
+}
+int cuda_check(Ctx& c) {
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) return LMVD_OK;
+  return latch(c, e == cudaErrorMemoryAllocation ? LMVD_ERR_OOM : LMVD_ERR_CUDA);
+}
+
+template <class T>
+int upload(Ctx& c, const std::vector<T>& h, T** d) {
+  if (cudaMalloc((void**)d, sizeof(T) * std::max<size_t>(1, h.size())) != cudaSuccess) return LMVD_ERR_OOM;
+  c.small_allocs.push_back(*d);
+  if (!h.empty() && cudaMemcpy(*d, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+    return LMVD_ERR_CUDA;
+  return LMVD_OK;
+}
+
+int upload_band(Ctx& c, const RowBand& m, DBand& d) {
+  int* c0;
+  double* v;
+  int e = upload(c, m.c0, &c0);
+  if (e) return e;
+  e = upload(c, m.v, &v);
+  if (e) return e;
+  d.c0 = c0;
+  d.v = v;
+  d.rows = m.rows;
+  d.w = m.w;
+  return LMVD_OK;
+}
+
+int half_width(const RowBand& m) {
+  int K = 0;
+  for (int i = 0; i < m.rows; ++i)
+    for (int q = 0; q < m.w; ++q)
+      if (m.v[(size_t)i * m.w + q] != 0.0) K = std::max(K, std::abs(m.c0[i] + q - i));
+  return K;
+}
+
+int upload_lu(Ctx& c, const BandLU& f, DLU& d) {
+  double *lo, *up, *invd;
+  int *nl, *nu;
+  int e = upload(c, f.lo, &lo);
+  if (!e) e = upload(c, f.up, &up);
+  if (!e) e = upload(c, f.invd, &invd);
+  if (!e) e = upload(c, f.nl, &nl);
+  if (!e) e = upload(c, f.nu, &nu);
+  if (e) return e;
+  d = DLU{lo, up, invd, nl, nu, f.n, f.K, 0};
+  return LMVD_OK;
+}
+
+// Band matrices A2 (k-independent part) and A0 (coefficient of -k^2) of the per-mode systems.
+struct PerMode {
+  DiagBand A2, A0;
+};
+
+// m^c system: rows 0 and ny: m2^c(-1) = m2^c(+1) = 0; rows 1..ny-1: (B*'' - k^2 B*) at g*_i.
+PerMode mc_system(const RowBand& Ss0, const RowBand& Ss2, int K) {
+  const int n = Ss0.rows;
+  PerMode p;
+  p.A2 = to_diag(Ss2, K);
+  p.A0 = to_diag(Ss0, K);
+  for (int r : {0, n - 1}) {
+    for (int q = -K; q <= K; ++q) {
+      int j = r + q;
+      if (j < 0 || j >= n) continue;
+      p.A2.el(r, j) = (q == 0) ? 1.0 : 0.0;
+      p.A0.el(r, j) = 0.0;
+    }
+  }
+  return p;
+}
+
+// m2^d update: rows 0, ny: m2 = 0; rows 1, ny-1: dm2/dy = 0 at -1, +1; rows 2..ny-2: (B*'' - k^2 B*) at g*_i.
+PerMode md_system(const RowBand& Ss0, const RowBand& Ss1, const RowBand& Ss2, int K) {
+  const int n = Ss0.rows;
+  PerMode p;
+  p.A2 = to_diag(Ss2, K);
+  p.A0 = to_diag(Ss0, K);
+  for (int r : {0, 1, n - 2, n - 1}) {
+    for (int q = -K; q <= K; ++q) {
+      int j = r + q;
+      if (j < 0 || j >= n) continue;
+      p.A0.el(r, j) = 0.0;
+      double v = 0.0;
+      if (r == 0 || r == n - 1) v = (q == 0) ? 1.0 : 0.0;
+      if (r == 1) v = Ss1.at(0, j);          // derivative at y0
+      if (r == n - 2) v = Ss1.at(n - 1, j);  // derivative at y1
+      p.A2.el(r, j) = v;
+    }
+  }
+  return p;
+}
+
+int factor_per_mode(Ctx& c, const PerMode& pm, int K, DLU& out) {
+  std::vector<int> nl, nu;
+  try {
+    band_profile(pm.A2, pm.A0, nl, nu);
+  } catch (const std::exception&) {
+    return LMVD_ERR_UNSUPPORTED;
+  }
+  const int n = pm.A2.n;
+  double *A2, *A0, *lo, *up, *invd;
+  int *dnl, *dnu;
+  int e = upload(c, pm.A2.a, &A2);
+  if (!e) e = upload(c, pm.A0.a, &A0);
+  if (!e) e = upload(c, nl, &dnl);
+  if (!e) e = upload(c, nu, &dnu);
+  if (e) return e;
+  const size_t M = c.g.M;
+  if (cudaMalloc(&lo, sizeof(double) * (size_t)n * K * M) != cudaSuccess) return LMVD_ERR_OOM;
+  c.small_allocs.push_back(lo);
+  if (cudaMalloc(&up, sizeof(double) * (size_t)n * K * M) != cudaSuccess) return LMVD_ERR_OOM;
+  c.small_allocs.push_back(up);
+  if (cudaMalloc(&invd, sizeof(double) * (size_t)n * M) != cudaSuccess) return LMVD_ERR_OOM;
+  c.small_allocs.push_back(invd);
+  k_factor<<<mode_blocks(c.g), TPB_MODE, 0, c.stream>>>(c.g, n, K, A2, A0, dnl, dnu, lo, up, invd);
+  out = DLU{lo, up, invd, dnl, dnu, n, K, M};
+  return cuda_check(c);
+}
+
+// ------------------------------------------------------------------ workspace arena
+struct Carver {
+  char* base;
+  size_t off = 0;
+  template <class T>
+  T* take(size_t count) {
+    off = (off + 255) & ~(size_t)255;
+    T* p = (T*)(base ? base + off : nullptr);
+    off += sizeof(T) * count;
+    return p;
+  }
+};
+
+void carve(Ctx& c, Carver& cv) {
+  const Grid& g = c.g;
+  const size_t S = (size_t)g.ny * g.M, Sp = (size_t)(g.ny + 1) * g.M, P = (size_t)g.ny * g.P;
+  const int ny = g.ny;
+  c.z = cv.take<cd>(S);
+  c.om = cv.take<cd>(S);
+  c.m2 = cv.take<cd>(Sp);
+  c.z_new = cv.take<cd>(S);
+  c.om_new = cv.take<cd>(S);
+  c.m2_new = cv.take<cd>(Sp);
+  for (auto& h : c.zh) h = cv.take<cd>(S);
+  c.zdot_prev = cv.take<cd>(S);
+  c.r_om_prev = cv.take<cd>(S);
+  c.r_phi_prev = cv.take<cd>(Sp);
+  c.Rz = cv.take<cd>(S);
+  c.zdot = cv.take<cd>(S);
+  c.rt = cv.take<cd>(S);
+  c.m1c = cv.take<cd>(S);
+  c.m2c = cv.take<cd>(Sp);
+  c.m3c = cv.take<cd>(S);
+  c.r_om = cv.take<cd>(S);
+  c.r_phi = cv.take<cd>(Sp);
+  for (auto& p : c.sv) p = cv.take<cd>(S);
+  for (auto& p : c.st) p = cv.take<cd>(S);
+  c.mm1 = cv.take<double>(ny);
+  c.mm3 = cv.take<double>(ny);
+  c.mm1_new = cv.take<double>(ny);
+  c.mm3_new = cv.take<double>(ny);
+  c.r_m = cv.take<double>(2 * ny);
+  c.r_m_prev = cv.take<double>(2 * ny);
+  for (auto& p : c.md) p = cv.take<double>(P);
+  c.rho = cv.take<double>(P);
+  c.invrho = cv.take<double>(P);
+  c.fprime = cv.take<double>(P);
+  for (auto& p : c.w) p = cv.take<double>(P);
+  for (auto& p : c.pw) p = cv.take<double>(P);
+  c.tbuf = cv.take<cd>((size_t)10 * ny * g.pz * (g.nx / 2));
+}
+
+// ------------------------------------------------------------------ substage pieces
+void eval_jobs(Ctx& c, std::initializer_list<EvalJob> jobs) {
+  EvalJobs ej{};
+  int n = 0;
+  for (const EvalJob& j : jobs) ej.j[n++] = j;
+  k_eval<<<dim3(mode_blocks(c.g), n), TPB_MODE, 0, c.stream>>>(c.g, ej);
+}
+
+void solve_interp(Ctx& c, std::initializer_list<SolveJob> jobs, const DLU& lu) {
+  SolveJobs sj{};
+  int n = 0;
+  for (const SolveJob& j : jobs) sj.j[n++] = j;
+  k_solve_shared<<<dim3(mode_blocks(c.g), n), TPB_MODE, 0, c.stream>>>(c.g, lu, sj);
+}
+
+// steps 1-2: m^d and z-derived fields in physical space; rho, 1/rho, f', grad z / rho; R_z
+void physical_pass_1(Ctx& c) {
+  Fields8 o{};
+  for (int f = 0; f < 8; ++f) o.p[f] = c.sv[f];
+  k_eval_p1<<<mode_blocks(c.g), TPB_MODE, 0, c.stream>>>(c.g, c.B0g, c.B1g, c.B2g, c.Sg0, c.Sg1, c.z, c.om, c.m2,
+                                                         c.mm1, c.mm3, o);
+  // physical: z, zx, zz, zy, lapz -> pw[0..4]; m^d -> md[0..2]
+  cd* in[8] = {c.sv[0], c.sv[1], c.sv[2], c.sv[3], c.sv[4], c.sv[5], c.sv[6], c.sv[7]};
+  double* out[8] = {c.pw[0], c.pw[1], c.pw[2], c.pw[3], c.pw[4], c.md[0], c.md[1], c.md[2]};
+  fft_inverse(c, in, out, 8);
+  const size_t n = (size_t)c.g.ny * c.g.P;
+  EosArgs e{c.cfg.rho_heavy, c.cfg.rho_light, 1.0 / (c.cfg.re * c.cfg.sc)};
+  k_products_p1<<<elem_blocks(n), 256, 0, c.stream>>>(n, e, c.pw[0], c.pw[1], c.pw[2], c.pw[3], c.pw[4], c.md[0],
+                                                      c.md[1], c.md[2], c.rho, c.invrho, c.fprime, c.w[0], c.w[1],
+                                                      c.w[2], c.pw[5]);
+  double* fin[1] = {c.pw[5]};
+  cd* fout[1] = {c.sv[0]};
+  fft_forward(c, fin, fout, 1);
+  solve_interp(c, {SolveJob{c.sv[0], nullptr, c.Rz}}, c.lu_interp);
+}
+
+// rho_t = P[f'(z) zdot] and m^c = C(rho_t) (B coefficients), then m^c on the physical grid in pw[0..2]
+void mc_from_zdot(Ctx& c) {
+  const size_t n = (size_t)c.g.ny * c.g.P;
+  eval_jobs(c, {EvalJob{c.B0g, c.zdot, c.sv[0]}});
+  {
+    cd* in[1] = {c.sv[0]};
+    double* out[1] = {c.pw[0]};
+    fft_inverse(c, in, out, 1);
+  }
+  k_product_rt<<<elem_blocks(n), 256, 0, c.stream>>>(n, c.fprime, c.pw[0], c.pw[1]);
+  {
+    double* in[1] = {c.pw[1]};
+    cd* out[1] = {c.sv[1]};
+    fft_forward(c, in, out, 1);
+  }
+  solve_interp(c, {SolveJob{c.sv[1], nullptr, c.rt}}, c.lu_interp);
+  k_mc_solve<<<mode_blocks(c.g), TPB_MODE, 0, c.stream>>>(c.g, c.lu_mc, c.Bs[1], c.dstar, c.rt, c.m1c, c.m2c, c.m3c);
+  eval_jobs(c, {EvalJob{c.B0g, c.m1c, c.sv[0]}, EvalJob{c.Sg0, c.m2c, c.sv[1]}, EvalJob{c.B0g, c.m3c, c.sv[2]}});
+  cd* in[3] = {c.sv[0], c.sv[1], c.sv[2]};
+  double* out[3] = {c.pw[0], c.pw[1], c.pw[2]};
+  fft_inverse(c, in, out, 3);
+}
+
+// one application of the fixed point (Eq. y_k): zdot <- L(z) zdot + R_z
+void fp_apply(Ctx& c) {
+  mc_from_zdot(c);
+  const size_t n = (size_t)c.g.ny * c.g.P;
+  k_product_L<<<elem_blocks(n), 256, 0, c.stream>>>(n, c.w[0], c.w[1], c.w[2], c.pw[0], c.pw[1], c.pw[2], c.pw[3]);
+  double* in[1] = {c.pw[3]};
+  cd* out[1] = {c.sv[3]};
+  fft_forward(c, in, out, 1);
+  solve_interp(c, {SolveJob{c.sv[3], c.Rz, c.zdot}}, c.lu_interp);
+}
+
+void startup(Ctx& c) {
+  const size_t S = (size_t)c.g.ny * c.g.M;
+  physical_pass_1(c);
+  cudaMemsetAsync(c.zdot, 0, sizeof(cd) * S, c.stream);
+  for (int it = 0; it < c.cfg.n_startup; ++it) fp_apply(c);
+  const double dt = c.cfg.dt;
+  k_backfill<<<elem_blocks(S), 256, 0, c.stream>>>(S, 0.5 * dt, dt, 1.5 * dt, c.z, c.zdot, c.zh[0], c.zh[1], c.zh[2]);
+  cudaMemcpyAsync(c.zdot_prev, c.zdot, sizeof(cd) * S, cudaMemcpyDeviceToDevice, c.stream);
+  cudaMemsetAsync(c.r_om_prev, 0, sizeof(cd) * S, c.stream);
+  cudaMemsetAsync(c.r_phi_prev, 0, sizeof(cd) * (S + c.g.M), c.stream);
+  cudaMemsetAsync(c.r_m_prev, 0, sizeof(double) * 2 * c.g.ny, c.stream);
+  c.s = 0;
+}
+
+int advance(Ctx& c) {
+  const Grid& g = c.g;
+  const lmvd_config& cf = c.cfg;
+  const size_t S = (size_t)g.ny * g.M;
+  const size_t n = (size_t)g.ny * g.P;
+  const bool stage_n = (c.s % 2) == 0;
+  // steps 1-2
+  physical_pass_1(c);
+  double a[4];
+  if (stage_n) {
+    const double b = cf.beta_n;
+    a[0] = 2.0; a[1] = -(2.0 + 0.5 * b); a[2] = b; a[3] = -0.5 * b;
+  } else {
+    const double b = cf.beta_p;
+    a[0] = 4.0 + b; a[1] = -(5.0 + 2.0 * b); a[2] = b; a[3] = 1.0;
+  }
+  k_bdf<<<elem_blocks(S), 256, 0, c.stream>>>(S, a[0], a[1], a[2], a[3], 1.0 / cf.dt, c.z, c.zh[0], c.zh[1], c.zh[2],
+                                              c.zdot);
+  // step 3
+  for (int k = 0; k < cf.kf; ++k) fp_apply(c);
+  mc_from_zdot(c);
+  // steps 4-5: products with m = m^d + m^c, forward transforms, RHS streams, collocation solves, RHS
+  P2Out q{};
+  for (int f = 0; f < 10; ++f) q.p[f] = c.pw[f];
+  k_products_p2<<<elem_blocks(n), 256, 0, c.stream>>>(n, c.md[0], c.md[1], c.md[2], c.pw[0], c.pw[1], c.pw[2], c.rho,
+                                                      c.invrho, q);
+  fft_forward(c, c.pw, c.sv, 10);
+  Fields10C svc{};
+  for (int f = 0; f < 10; ++f) svc.p[f] = c.sv[f];
+  Fields7 stw{};
+  for (int f = 0; f < 7; ++f) stw.p[f] = c.st[f];
+  k_rhs_combine<<<elem_blocks(S), 256, 0, c.stream>>>(g, 1.0 / cf.re, 1.0 / (cf.fr * cf.fr), svc, stw);
+  solve_interp(c,
+               {SolveJob{c.st[1], nullptr, c.st[1]}, SolveJob{c.st[2], nullptr, c.st[2]},
+                SolveJob{c.st[3], nullptr, c.st[3]}, SolveJob{c.st[4], nullptr, c.st[4]},
+                SolveJob{c.st[5], nullptr, c.st[5]}, SolveJob{c.st[6], nullptr, c.st[6]}},
+               c.lu_interp);
+  Fields7C stc{};
+  for (int f = 0; f < 7; ++f) stc.p[f] = c.st[f];
+  k_rhs_eval<<<mode_blocks(g), TPB_MODE, 0, c.stream>>>(g, c.B1g, c.B2g, c.Bs[0], c.Bs[1], c.Bs[2], c.Bs[3], stc,
+                                                        c.r_om, c.r_phi, c.r_m);
+  // step 6: midpoint RK2, low-storage: (al, be) = (1/2, 0) at stage n, (1, -1/2) at stage '
+  UpdateArgs u{};
+  u.dt = cf.dt;
+  u.al = stage_n ? 0.5 : 1.0;
+  u.be = stage_n ? 0.0 : -0.5;
+  u.om = c.om; u.r_om = c.r_om; u.r_om_prev = c.r_om_prev;
+  u.z = c.z; u.zdot = c.zdot; u.zdot_prev = c.zdot_prev;
+  u.m2 = c.m2; u.r_phi = c.r_phi; u.r_phi_prev = c.r_phi_prev;
+  u.mm1 = c.mm1; u.mm3 = c.mm3; u.r_m = c.r_m; u.r_m_prev = c.r_m_prev;
+  u.om_new = c.om_new; u.z_new = c.z_new; u.m2_new = c.m2_new; u.mm1_new = c.mm1_new; u.mm3_new = c.mm3_new;
+  k_update_om_z<<<dim3(mode_blocks(g), 2), TPB_MODE, 0, c.stream>>>(g, c.B0g, c.lu_interp, c.lu_neumann, u);
+  k_update_means<<<1, 32, 0, c.stream>>>(g, c.B0g, c.lu_interp, u);
+  k_update_m2<<<mode_blocks(g), TPB_MODE, 0, c.stream>>>(g, c.Ss0, c.Ss2, c.lu_md, u);
+  // history rotation (pointer swaps)
+  cd* oldest = c.zh[2];
+  c.zh[2] = c.zh[1];
+  c.zh[1] = c.zh[0];
+  c.zh[0] = c.z;
+  c.z = c.z_new;
+  c.z_new = oldest;
+  std::swap(c.om, c.om_new);
+  std::swap(c.m2, c.m2_new);
+  std::swap(c.mm1, c.mm1_new);
+  std::swap(c.mm3, c.mm3_new);
+  std::swap(c.zdot_prev, c.zdot);
+  std::swap(c.r_om_prev, c.r_om);
+  std::swap(c.r_phi_prev, c.r_phi);
+  std::swap(c.r_m_prev, c.r_m);
+  c.s += 1;
+  return cuda_check(c);
+}
+
+bool valid_cfg(const lmvd_config& f) {
+  if (f.nx < 4 || f.nz < 4 || (f.nx % 2) || (f.nz % 2)) return false;
+  if (f.spline_order < 4 || f.spline_order > 8 || f.ny < f.spline_order + 4) return false;
+  if (!(f.lx > 0) || !(f.lz > 0) || !(f.y1 > f.y0)) return false;
+  if (!(f.re > 0) || !(f.sc > 0) || !(f.fr > 0) || !(f.rho_heavy > 0) || !(f.rho_light > 0)) return false;
+  if (!(f.dt > 0) || f.kf < 0 || f.n_startup < 0) return false;
+  return true;
+}
+
+int copy_in(Ctx& c, void* dst, const void* src, size_t bytes) {
+  return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, c.stream) == cudaSuccess ? LMVD_OK : LMVD_ERR_CUDA;
+}
+
+}  // namespace
+
+// ====================================================================== C-ABI
+extern "C" {
+
+int lmvd_default_config(lmvd_config* f, int nx, int ny, int nz) {
+  if (!f) return LMVD_ERR_INVALID_ARG;
+  std::memset(f, 0, sizeof(*f));
+  f->nx = nx;
+  f->ny = ny;
+  f->nz = nz;
+  f->spline_order = 6;
+  f->lx = f->lz = 6.283185307179586476925286766559;
+  f->y0 = -1.0;
+  f->y1 = 1.0;
+  f->re = 1000.0;
+  f->sc = 1.0;
+  f->fr = 1.0;
+  f->rho_heavy = 1.0;
+  f->rho_light = 1.0 / 3.0;
+  f->dt = 1e-3;
+  f->kf = 4;
+  f->beta_n = 0.0;
+  f->beta_p = -4.0;
+  f->n_startup = 20;
+  return LMVD_OK;
+}
+
+int lmvd_create(const lmvd_config* cfg, void* stream, lmvd_ctx** out) {
+  if (!cfg || !out) return LMVD_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!valid_cfg(*cfg)) return LMVD_ERR_INVALID_ARG;
+  lmvd_ctx* h = new (std::nothrow) lmvd_ctx();
+  if (!h) return LMVD_ERR_OOM;
+  Ctx& c = h->c;
+  c.cfg = *cfg;
+  c.stream = (cudaStream_t)stream;
+  Grid& g = c.g;
+  g.nx = cfg->nx;
+  g.ny = cfg->ny;
+  g.nz = cfg->nz;
+  g.nxh = cfg->nx / 2 + 1;
+  g.px = 3 * cfg->nx / 2;
+  g.pz = 3 * cfg->nz / 2;
+  g.M = (size_t)cfg->nz * g.nxh;
+  g.P = (size_t)g.px * g.pz;
+  g.lx = cfg->lx;
+  g.lz = cfg->lz;
+  int err = LMVD_OK;
+  try {
+    const int p = cfg->spline_order, ny = cfg->ny;
+    Knots kb = clamped_uniform(p, ny, cfg->y0, cfg->y1);
+    Knots ks = clamped_uniform(p + 1, ny + 1, cfg->y0, cfg->y1);
+    std::vector<double> gb = greville(kb), gs = greville(ks);
+    RowBand B0g = collocation(kb, gb, 0), B1g = collocation(kb, gb, 1), B2g = collocation(kb, gb, 2);
+    RowBand Bs[4];
+    for (int d = 0; d < 4; ++d) Bs[d] = collocation(kb, gs, d);
+    RowBand Sg0 = collocation(ks, gb, 0), Sg1 = collocation(ks, gb, 1);
+    RowBand Ss0 = collocation(ks, gs, 0), Ss1 = collocation(ks, gs, 1), Ss2 = collocation(ks, gs, 2);
+    // exact derivative map D*: (D* c)_i = (order-1) (c_{i+1} - c_i) / (t*_{i+order} - t*_{i+1})
+    std::vector<double> ds(ny);
+    for (int i = 0; i < ny; ++i) ds[i] = (double)p / (ks.t[i + p + 1] - ks.t[i + 1]);
+    if (!err) err = upload_band(c, B0g, c.B0g);
+    if (!err) err = upload_band(c, B1g, c.B1g);
+    if (!err) err = upload_band(c, B2g, c.B2g);
+    for (int d = 0; d < 4 && !err; ++d) err = upload_band(c, Bs[d], c.Bs[d]);
+    if (!err) err = upload_band(c, Sg0, c.Sg0);
+    if (!err) err = upload_band(c, Sg1, c.Sg1);
+    if (!err) err = upload_band(c, Ss0, c.Ss0);
+    if (!err) err = upload_band(c, Ss2, c.Ss2);
+    if (!err) err = upload(c, ds, &c.dstar);
+    // shared LUs: interpolation / Dirichlet (values at g) and Neumann (dz/dy rows at the walls)
+    const int Kb = std::max(half_width(B0g), half_width(B1g));
+    if (Kb > KMAX) throw std::runtime_error("band");
+    DiagBand Ai = to_diag(B0g, Kb), An = to_diag(B0g, Kb);
+    for (int r : {0, ny - 1})
+      for (int q = -Kb; q <= Kb; ++q) {
+        int j = r + q;
+        if (j >= 0 && j < ny) An.el(r, j) = B1g.at(r, j);
+      }
+    if (!err) err = upload_lu(c, band_lu(Ai), c.lu_interp);
+    if (!err) err = upload_lu(c, band_lu(An), c.lu_neumann);
+    // per-mode LUs of the m^c and m2^d systems
+    const int Ks = std::max({half_width(Ss0), half_width(Ss1), half_width(Ss2)});
+    if (Ks > KMAX) throw std::runtime_error("band");
+    if (!err) err = factor_per_mode(c, mc_system(Ss0, Ss2, Ks), Ks, c.lu_mc);
+    if (!err) err = factor_per_mode(c, md_system(Ss0, Ss1, Ss2, Ks), Ks, c.lu_md);
+  } catch (const std::exception&) {
+    err = err ? err : LMVD_ERR_UNSUPPORTED;
+  }
+  if (!err) err = fft_prepare(c);
+  if (!err) {
+    Carver probe{nullptr};
+    carve(c, probe);
+    c.arena_bytes = probe.off;
+    if (cudaMalloc(&c.arena, c.arena_bytes) != cudaSuccess) {
+      cudaGetLastError();
+      err = LMVD_ERR_OOM;
+    } else {
+      cudaMemsetAsync(c.arena, 0, c.arena_bytes, c.stream);
+      Carver real{(char*)c.arena};
+      carve(c, real);
+    }
+  }
+  if (!err && cudaStreamSynchronize(c.stream) != cudaSuccess) err = LMVD_ERR_CUDA;
+  if (err) {
+    lmvd_destroy(h);
+    return err;
+  }
+  *out = h;
+  return LMVD_OK;
+}
+
+void lmvd_destroy(lmvd_ctx* h) {
+  if (!h) return;
+  Ctx& c = h->c;
+  if (c.stream) cudaStreamSynchronize(c.stream);
+  else cudaDeviceSynchronize();
+  for (void* p : c.small_allocs) cudaFree(p);
+  if (c.arena) cudaFree(c.arena);
+  delete h;
+}
+
+size_t lmvd_history_bytes(const lmvd_ctx* h) {
+  if (!h) return 0;
+  const Grid& g = h->c.g;
+  return 16 + sizeof(cd) * g.M * ((size_t)6 * g.ny + 1) + sizeof(double) * 2 * g.ny;
+}
+
+int lmvd_set_state(lmvd_ctx* h, const void* z, const void* om, const void* m2, const double* mm1, const double* mm3,
+                   const void* history) {
+  if (!h || !z || !om || !m2 || !mm1 || !mm3) return LMVD_ERR_INVALID_ARG;
+  Ctx& c = h->c;
+  const Grid& g = c.g;
+  const size_t S = sizeof(cd) * g.ny * g.M, Sp = sizeof(cd) * (g.ny + 1) * g.M, R = sizeof(double) * g.ny;
+  int e = copy_in(c, c.z, z, S);
+  if (!e) e = copy_in(c, c.om, om, S);
+  if (!e) e = copy_in(c, c.m2, m2, Sp);
+  if (!e) e = copy_in(c, c.mm1, mm1, R);
+  if (!e) e = copy_in(c, c.mm3, mm3, R);
+  if (e) return latch(c, e);
+  k_sanitize<<<elem_blocks(g.ny * g.M), 256, 0, c.stream>>>(g, g.ny, c.z, 0);
+  k_sanitize<<<elem_blocks(g.ny * g.M), 256, 0, c.stream>>>(g, g.ny, c.om, 1);
+  k_sanitize<<<elem_blocks((g.ny + 1) * g.M), 256, 0, c.stream>>>(g, g.ny + 1, c.m2, 1);
+  if (!history) {
+    startup(c);
+    return cuda_check(c);
+  }
+  const char* hb = (const char*)history;
+  long long s = 0;
+  if (cudaMemcpy(&s, hb, sizeof(s), cudaMemcpyDefault) != cudaSuccess) return latch(c, LMVD_ERR_CUDA);
+  if (s < 0) return LMVD_ERR_INVALID_ARG;
+  size_t off = 16;
+  for (int q = 0; q < 3 && !e; ++q, off += S) e = copy_in(c, c.zh[q], hb + off, S);
+  if (!e) { e = copy_in(c, c.zdot_prev, hb + off, S); off += S; }
+  if (!e) { e = copy_in(c, c.r_om_prev, hb + off, S); off += S; }
+  if (!e) { e = copy_in(c, c.r_phi_prev, hb + off, Sp); off += Sp; }
+  if (!e) e = copy_in(c, c.r_m_prev, hb + off, 2 * R);
+  if (e) return latch(c, e);
+  c.s = (int)s;
+  return cuda_check(c);
+}
+
+int lmvd_get_state(lmvd_ctx* h, void* z, void* om, void* m2, double* mm1, double* mm3, void* history) {
+  if (!h) return LMVD_ERR_INVALID_ARG;
+  Ctx& c = h->c;
+  const Grid& g = c.g;
+  const size_t S = sizeof(cd) * g.ny * g.M, Sp = sizeof(cd) * (g.ny + 1) * g.M, R = sizeof(double) * g.ny;
+  int e = LMVD_OK;
+  if (z && !e) e = copy_in(c, z, c.z, S);
+  if (om && !e) e = copy_in(c, om, c.om, S);
+  if (m2 && !e) e = copy_in(c, m2, c.m2, Sp);
+  if (mm1 && !e) e = copy_in(c, mm1, c.mm1, R);
+  if (mm3 && !e) e = copy_in(c, mm3, c.mm3, R);
+  if (history && !e) {
+    char* hb = (char*)history;
+    h->s_blob = c.s;
+    e = copy_in(c, hb, &h->s_blob, sizeof(long long));
+    size_t off = 16;
+    for (int q = 0; q < 3 && !e; ++q, off += S) e = copy_in(c, hb + off, c.zh[q], S);
+    if (!e) { e = copy_in(c, hb + off, c.zdot_prev, S); off += S; }
+    if (!e) { e = copy_in(c, hb + off, c.r_om_prev, S); off += S; }
+    if (!e) { e = copy_in(c, hb + off, c.r_phi_prev, Sp); off += Sp; }
+    if (!e) e = copy_in(c, hb + off, c.r_m_prev, 2 * R);
+  }
+  return e ? latch(c, e) : LMVD_OK;
+}
+
+int lmvd_advance_substage(lmvd_ctx* h) {
+  if (!h) return LMVD_ERR_INVALID_ARG;
+  return advance(h->c);
+}
+
+int lmvd_step(lmvd_ctx* h, int nsteps) {
+  if (!h || nsteps < 0) return LMVD_ERR_INVALID_ARG;
+  for (int i = 0; i < 2 * nsteps; ++i) {
+    int e = advance(h->c);
+    if (e) return e;
+  }
+  return LMVD_OK;
+}
+
+size_t lmvd_field_bytes(const lmvd_ctx* h, int which) {
+  if (!h) return 0;
+  const Grid& g = h->c.g;
+  switch (which) {
+    case LMVD_FIELD_MC2:
+    case LMVD_FIELD_R_PHI2: return sizeof(cd) * (g.ny + 1) * g.M;
+    case LMVD_FIELD_R_MEANS: return sizeof(double) * 2 * g.ny;
+    case LMVD_FIELD_RZ:
+    case LMVD_FIELD_ZDOT:
+    case LMVD_FIELD_RHO_T:
+    case LMVD_FIELD_MC1:
+    case LMVD_FIELD_MC3:
+    case LMVD_FIELD_R_OMEGA2: return sizeof(cd) * g.ny * g.M;
+    default: return 0;
+  }
+}
+
+int lmvd_get_field(lmvd_ctx* h, int which, void* out) {
+  if (!h || !out) return LMVD_ERR_INVALID_ARG;
+  Ctx& c = h->c;
+  const void* src = nullptr;
+  switch (which) {
+    case LMVD_FIELD_RZ: src = c.Rz; break;
+    case LMVD_FIELD_ZDOT: src = c.s > 0 ? c.zdot_prev : c.zdot; break;
+    case LMVD_FIELD_RHO_T: src = c.rt; break;
+    case LMVD_FIELD_MC1: src = c.m1c; break;
+    case LMVD_FIELD_MC2: src = c.m2c; break;
+    case LMVD_FIELD_MC3: src = c.m3c; break;
+    case LMVD_FIELD_R_OMEGA2: src = c.r_om_prev; break;
+    case LMVD_FIELD_R_PHI2: src = c.r_phi_prev; break;
+    case LMVD_FIELD_R_MEANS: src = c.r_m_prev; break;
+    default: return LMVD_ERR_INVALID_ARG;
+  }
+  int e = copy_in(c, out, src, lmvd_field_bytes(h, which));
+  return e ? latch(c, e) : LMVD_OK;
+}
+
+int lmvd_substage_index(const lmvd_ctx* h) { return h ? h->c.s : -1; }
+
+int lmvd_synchronize(lmvd_ctx* h) {
+  if (!h) return LMVD_ERR_INVALID_ARG;
+  Ctx& c = h->c;
+  if (cudaStreamSynchronize(c.stream) != cudaSuccess) return latch(c, LMVD_ERR_CUDA);
+  cuda_check(c);
+  return c.status;
+}
+
+int lmvd_status(const lmvd_ctx* h) { return h ? h->c.status : LMVD_ERR_INVALID_ARG; }
+
+const char* lmvd_strerror(int code) {
+  switch (code) {
+    case LMVD_OK: return "ok";
+    case LMVD_ERR_INVALID_ARG: return "invalid argument";
+    case LMVD_ERR_CUDA: return "CUDA error";
+    case LMVD_ERR_OOM: return "device out of memory";
+    case LMVD_ERR_NONFINITE: return "non-finite value in the state";
+    case LMVD_ERR_UNSUPPORTED: return "unsupported configuration";
+    default: return "unknown error";
+  }
+}
+
+}  // extern "C"

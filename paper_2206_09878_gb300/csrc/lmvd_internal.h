@@ -1,0 +1,131 @@
+// Internal definitions shared by the CUDA translation units of liblmvd.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+#include "../../include/lmvd.h"
+
+namespace lmvd {
+
+constexpr int KMAX = 8;   // widest band (each side) of any y-system LU supported
+constexpr int WMAX = 9;   // widest row of a collocation matrix (spline order <= 9)
+
+// ---------------------------------------------------------------- complex helpers (FP64)
+struct cd {
+  double re, im;
+};
+__host__ __device__ inline cd mk(double r, double i) { return cd{r, i}; }
+__host__ __device__ inline cd operator+(cd a, cd b) { return cd{a.re + b.re, a.im + b.im}; }
+__host__ __device__ inline cd operator-(cd a, cd b) { return cd{a.re - b.re, a.im - b.im}; }
+__host__ __device__ inline cd operator*(double s, cd a) { return cd{s * a.re, s * a.im}; }
+__host__ __device__ inline cd cmul(cd a, cd b) { return cd{a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
+__host__ __device__ inline cd conj(cd a) { return cd{a.re, -a.im}; }
+__host__ __device__ inline cd times_i(cd a) { return cd{-a.im, a.re}; }         // i * a
+__host__ __device__ inline cd fma_rc(double s, cd x, cd acc) { return cd{fma(s, x.re, acc.re), fma(s, x.im, acc.im)}; }
+
+// ---------------------------------------------------------------- y-operators in device memory
+// Row-banded collocation matrix: row i covers columns c0[i] .. c0[i] + w - 1.
+struct DBand {
+  const int* c0;
+  const double* v;
+  int rows, w;
+};
+// LU factors of band systems. Shared factors: mstride = 0; per-mode factors: mstride = #modes and
+// element (i, q) of mode m at [(i * K + q) * mstride + m].
+struct DLU {
+  const double* lo;
+  const double* up;
+  const double* invd;
+  const int* nl;
+  const int* nu;
+  int n, K;
+  size_t mstride;
+};
+
+// Spectral field: complex [rows][nz][nxh], mode index m = jz * nxh + kx, M = nz * nxh.
+struct Grid {
+  int nx, ny, nz, nxh, px, pz;
+  size_t M;      // modes per y-row
+  size_t P;      // physical points per plane = px * pz
+  double lx, lz;
+};
+
+__device__ inline bool is_nyquist(const Grid& g, int m) {
+  int kx = m % g.nxh, jz = m / g.nxh;
+  return kx == g.nx / 2 || jz == g.nz / 2;
+}
+__device__ inline void wavenumbers(const Grid& g, int m, double& k1, double& k3) {
+  int kx = m % g.nxh, jz = m / g.nxh;
+  int kz = jz < g.nz / 2 ? jz : jz - g.nz;
+  k1 = 6.283185307179586476925286766559 / g.lx * kx;
+  k3 = 6.283185307179586476925286766559 / g.lz * kz;
+}
+
+__device__ inline cd band_row(const DBand& B, int i, const cd* x, size_t M, int m) {
+  const int c = B.c0[i];
+  const double* v = B.v + (size_t)i * B.w;
+  cd acc = mk(0, 0);
+  for (int q = 0; q < B.w; ++q) acc = fma_rc(__ldg(v + q), x[(size_t)(c + q) * M + m], acc);
+  return acc;
+}
+
+// ---------------------------------------------------------------- FFT plan
+struct FFTPlan {
+  int n = 0;
+  int nst = 0;
+  int radix[24];
+  double2* tw = nullptr;   // tw[m] = (cos 2 pi m / n, sin 2 pi m / n), device
+  int batch = 1;           // transforms per CTA
+};
+
+// ---------------------------------------------------------------- context
+struct Ctx {
+  lmvd_config cfg;
+  Grid g;
+  cudaStream_t stream = nullptr;
+  int s = 0;               // substage counter (even: stage n, odd: stage ')
+  int status = 0;
+
+  // operators
+  DBand B0g, B1g, B2g, Bs[4], Sg0, Sg1, Ss0, Ss2;
+  double* dstar = nullptr;  // ny entries: (D* c)_i = dstar[i] (c_{i+1} - c_i)
+  DLU lu_interp, lu_neumann, lu_mc, lu_md;
+  double* A2mc = nullptr; double* A0mc = nullptr; double* A2md = nullptr; double* A0md = nullptr;
+  int Kmc = 0, Kmd = 0;
+  FFTPlan fx, fz;
+
+  // memory arena
+  void* arena = nullptr;
+  size_t arena_bytes = 0;
+  std::vector<void*> small_allocs;
+
+  // state and history (spectral, B coefficients)
+  cd *z, *om, *m2;
+  double *mm1, *mm3;
+  cd* zh[3];
+  cd *zdot_prev, *r_om_prev, *r_phi_prev;
+  double* r_m_prev;  // 2 * ny
+  // substage work (spectral)
+  cd *z_new, *om_new, *m2_new;
+  double *mm1_new, *mm3_new;
+  cd *Rz, *zdot, *rt, *m1c, *m2c, *m3c, *r_om, *r_phi;
+  double* r_m;        // 2 * ny
+  cd* sv[10];         // spectral value fields at g (FFT outputs / inputs)
+  cd* st[7];          // RHS streams
+  cd* tbuf;           // FFT intermediate: up to 10 fields of ny * pz * (nx/2)
+  // physical
+  double *md[3], *rho, *invrho, *fprime, *w[3];
+  double* pw[10];     // physical work fields
+};
+
+// ---------------------------------------------------------------- launchers (defined in .cu files)
+int fft_prepare(Ctx& c);                       // plans, twiddles, smem attributes
+// inverse: nf spectral value fields (in[f]) -> physical (out[f])
+void fft_inverse(Ctx& c, cd* const* in, double* const* out, int nf);
+// forward: nf physical fields -> spectral value fields, truncated and scaled
+void fft_forward(Ctx& c, double* const* in, cd* const* out, int nf);
+
+}  // namespace lmvd

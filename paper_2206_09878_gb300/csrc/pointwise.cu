@@ -1,0 +1,65 @@
+// Physical-space products on the 3/2-padded grid (one thread per grid point, grid-stride).
+//
+// Paper Sec. 2.1 (R_z, L), Sec. 4.3 (applying L: rho_t = f'(z) dz/dt, then -(1/rho) grad z . m^c),
+// Eq. om / phi (C_ij = -rho u_i u_j), Sec. 5 (binary-mixing EOS rho = rl rh / (rh - (rh - rl) z)).
+// 1/rho is linear in z, so the EOS needs one division per point (rho itself, used by gravity).
+#include "ykernels.h"
+
+namespace lmvd {
+
+// rho, 1/rho, f'(z) = rho^2 (rh - rl) / (rl rh), w = grad z / rho, and
+// R_z = (-m^d . grad z + (rho D_z) lap z) / rho with rho D_z = kappa constant (Sc = 1 setting).
+__global__ void k_products_p1(size_t n, EosArgs e, const double* zp, const double* zx, const double* zz,
+                              const double* zy, const double* lapz, const double* m1, const double* m2,
+                              const double* m3, double* rho, double* invrho, double* fprime, double* w1, double* w2,
+                              double* w3, double* rz) {
+  const double irlrh = 1.0 / (e.rl * e.rh);
+  const double drho = e.rh - e.rl;
+  for (size_t o = blockIdx.x * (size_t)blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x) {
+    const double ir = (e.rh - drho * zp[o]) * irlrh;
+    const double r = 1.0 / ir;
+    const double gx = zx[o], gy = zy[o], gz = zz[o];
+    rho[o] = r;
+    invrho[o] = ir;
+    fprime[o] = r * r * drho * irlrh;
+    w1[o] = gx * ir;
+    w2[o] = gy * ir;
+    w3[o] = gz * ir;
+    rz[o] = (e.kappa * lapz[o] - (m1[o] * gx + m2[o] * gy + m3[o] * gz)) * ir;
+  }
+}
+
+// rho_t = f'(z) dz/dt
+__global__ void k_product_rt(size_t n, const double* fprime, const double* zdot, double* out) {
+  for (size_t o = blockIdx.x * (size_t)blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x)
+    out[o] = fprime[o] * zdot[o];
+}
+
+// L tail: -(1/rho) grad z . m^c
+__global__ void k_product_L(size_t n, const double* w1, const double* w2, const double* w3, const double* m1,
+                            const double* m2, const double* m3, double* out) {
+  for (size_t o = blockIdx.x * (size_t)blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x)
+    out[o] = -(w1[o] * m1[o] + w2[o] * m2[o] + w3[o] * m3[o]);
+}
+
+// m = m^d + m^c; outputs C11, C12, C13, C22, C23, C33 (C_ij = -m_i m_j / rho), u1, u2, u3 (u = m / rho), rho
+__global__ void k_products_p2(size_t n, const double* md1, const double* md2, const double* md3, const double* mc1,
+                              const double* mc2, const double* mc3, const double* rho, const double* invrho, P2Out q) {
+  for (size_t o = blockIdx.x * (size_t)blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x) {
+    const double ir = invrho[o];
+    const double a = md1[o] + mc1[o], b = md2[o] + mc2[o], c = md3[o] + mc3[o];
+    const double ua = a * ir, ub = b * ir, uc = c * ir;
+    q.p[0][o] = -a * ua;
+    q.p[1][o] = -a * ub;
+    q.p[2][o] = -a * uc;
+    q.p[3][o] = -b * ub;
+    q.p[4][o] = -b * uc;
+    q.p[5][o] = -c * uc;
+    q.p[6][o] = ua;
+    q.p[7][o] = ub;
+    q.p[8][o] = uc;
+    q.p[9][o] = rho[o];
+  }
+}
+
+}  // namespace lmvd

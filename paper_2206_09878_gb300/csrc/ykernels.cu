@@ -1,0 +1,421 @@
+// Kernels along the inhomogeneous direction y: one thread per Fourier mode (kx, kz) walks the
+// B-spline rows, so a warp reads 32 consecutive modes of one row (coalesced, [y][kz][kx] layout).
+//
+// Paper: Sec. 4.1 (m^d, Eq. phi_poisson, md_recon), Sec. 4.2 (m^c, Eq. COM_fourier, CF_fourier,
+// mc_recon, mc_mean), Sec. 4.4 (Eq. DNS_system, Algorithm 2), Sec. 3.2-3.3 (Eq. dzdt_guesses,
+// midpoint RK2), Appendix C (B-spline spaces and the exact derivative map D*).
+#include "ykernels.h"
+
+namespace lmvd {
+
+// ------------------------------------------------------------------ band LU access
+__device__ inline double lu_lo(const DLU& f, int i, int q, int m) {
+  return __ldg(f.lo + (f.mstride ? ((size_t)(i * f.K + q - 1) * f.mstride + m) : (size_t)(i * f.K + q - 1)));
+}
+__device__ inline double lu_up(const DLU& f, int i, int r, int m) {
+  return __ldg(f.up + (f.mstride ? ((size_t)(i * f.K + r - 1) * f.mstride + m) : (size_t)(i * f.K + r - 1)));
+}
+__device__ inline double lu_invd(const DLU& f, int i, int m) {
+  return __ldg(f.invd + (f.mstride ? ((size_t)i * f.mstride + m) : (size_t)i));
+}
+
+// Forward then backward substitution of L U x = rhs for mode m.
+// rhs(i) gives row i of the right-hand side; y is scratch of n rows (stride M) that may alias the
+// output; out(i, x_i, x_{i+1}) receives the solution in decreasing i.
+template <class Rhs, class Out>
+__device__ void band_solve(const DLU& f, int m, cd* y, size_t M, Rhs rhs, Out out) {
+  cd win[KMAX];
+#pragma unroll
+  for (int q = 0; q < KMAX; ++q) win[q] = mk(0, 0);
+  for (int i = 0; i < f.n; ++i) {
+    cd v = rhs(i);
+    const int nl = __ldg(f.nl + i);
+#pragma unroll
+    for (int q = 1; q <= KMAX; ++q)
+      if (q <= nl) v = fma_rc(-lu_lo(f, i, q, m), win[q - 1], v);
+#pragma unroll
+    for (int q = KMAX - 1; q > 0; --q) win[q] = win[q - 1];
+    win[0] = v;
+    y[(size_t)i * M + m] = v;
+  }
+#pragma unroll
+  for (int q = 0; q < KMAX; ++q) win[q] = mk(0, 0);
+  for (int i = f.n - 1; i >= 0; --i) {
+    cd v = y[(size_t)i * M + m];
+    const int nu = __ldg(f.nu + i);
+#pragma unroll
+    for (int r = 1; r <= KMAX; ++r)
+      if (r <= nu) v = fma_rc(-lu_up(f, i, r, m), win[r - 1], v);
+    v = lu_invd(f, i, m) * v;
+    out(i, v, win[0]);
+#pragma unroll
+    for (int q = KMAX - 1; q > 0; --q) win[q] = win[q - 1];
+    win[0] = v;
+  }
+}
+
+__device__ inline double band_row_real(const DBand& B, int i, const double* x) {
+  const int c = B.c0[i];
+  const double* v = B.v + (size_t)i * B.w;
+  double acc = 0.0;
+  for (int q = 0; q < B.w; ++q) acc = fma(__ldg(v + q), x[c + q], acc);
+  return acc;
+}
+
+// ------------------------------------------------------------------ step 1-2 inputs: values at g
+// out[0..7] = z, dz/dx, dz/dz, dz/dy, lap z, m1^d, m2^d, m3^d at the Greville points of the order-p space.
+// m1^d, m3^d follow Eq. md_recon with d m2^d / dy evaluated directly from the order-(p+1) space;
+// the k = 0 mode carries the plane means (and m2^d = 0).
+__global__ void k_eval_p1(Grid g, DBand B0g, DBand B1g, DBand B2g, DBand Sg0, DBand Sg1, const cd* z,
+                          const cd* om, const cd* m2, const double* mm1, const double* mm3, Fields8 out) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= (int)g.M) return;
+  const size_t M = g.M;
+  if (is_nyquist(g, m)) {
+    for (int i = 0; i < g.ny; ++i)
+      for (int f = 0; f < 8; ++f) out.p[f][(size_t)i * M + m] = mk(0, 0);
+    return;
+  }
+  double k1, k3;
+  wavenumbers(g, m, k1, k3);
+  const double k2 = k1 * k1 + k3 * k3;
+  const double ik2 = m == 0 ? 0.0 : 1.0 / k2;
+  for (int i = 0; i < g.ny; ++i) {
+    const size_t o = (size_t)i * M + m;
+    const cd zg = band_row(B0g, i, z, M, m);
+    const cd zy = band_row(B1g, i, z, M, m);
+    const cd zyy = band_row(B2g, i, z, M, m);
+    out.p[0][o] = zg;
+    out.p[1][o] = k1 * times_i(zg);
+    out.p[2][o] = k3 * times_i(zg);
+    out.p[3][o] = zy;
+    out.p[4][o] = (-k2) * zg + zyy;
+    if (m == 0) {
+      out.p[5][o] = mk(band_row_real(B0g, i, mm1), 0.0);
+      out.p[6][o] = mk(0, 0);
+      out.p[7][o] = mk(band_row_real(B0g, i, mm3), 0.0);
+    } else {
+      const cd dm2 = band_row(Sg1, i, m2, M, m);
+      const cd omg = band_row(B0g, i, om, M, m);
+      out.p[5][o] = ik2 * times_i(k1 * dm2 - k3 * omg);
+      out.p[6][o] = band_row(Sg0, i, m2, M, m);
+      out.p[7][o] = ik2 * times_i(k3 * dm2 + k1 * omg);
+    }
+  }
+}
+
+// ------------------------------------------------------------------ generic values at points
+// job blockIdx.y: out = B in (rows B.rows), Nyquist modes zero.
+__global__ void k_eval(Grid g, EvalJobs jobs) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= (int)g.M) return;
+  const EvalJob& jb = jobs.j[blockIdx.y];
+  const size_t M = g.M;
+  const bool ny = is_nyquist(g, m);
+  for (int i = 0; i < jb.B.rows; ++i)
+    jb.out[(size_t)i * M + m] = ny ? mk(0, 0) : band_row(jb.B, i, jb.in, M, m);
+}
+
+// ------------------------------------------------------------------ shared-factor solves
+// field blockIdx.y: out = A^{-1} in (+ add); used for collocation (interpolation) solves.
+__global__ void k_solve_shared(Grid g, DLU lu, SolveJobs jobs) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= (int)g.M) return;
+  const SolveJob& jb = jobs.j[blockIdx.y];
+  const size_t M = g.M;
+  if (is_nyquist(g, m)) {
+    for (int i = 0; i < lu.n; ++i) jb.out[(size_t)i * M + m] = mk(0, 0);
+    return;
+  }
+  const cd* in = jb.in;
+  const cd* add = jb.add;
+  cd* out = jb.out;
+  band_solve(
+      lu, m, out, M, [&](int i) { return in[(size_t)i * M + m]; },
+      [&](int i, cd x, cd) { out[(size_t)i * M + m] = add ? x + add[(size_t)i * M + m] : x; });
+}
+
+// ------------------------------------------------------------------ m^c from rho_t
+// Eq. COM_fourier + CF_fourier with m_par eliminated: rows 1..ny-1 collocate
+// (B*'' - k^2 B*) m2^c = -B' rho_t at the interior order-(p+1) Greville points, rows 0 and ny set
+// m2^c(+-1) = 0 (walls). Then m_par = i (rho_t + D* m2^c) / k (exact mass conservation in
+// B-coefficient space) and Eq. mc_recon m1^c = k1/k m_par, m3^c = k3/k m_par.
+// k = 0 (Eq. mc_mean): D* <m2^c> = -<rho_t> with <m2^c>(+1) = 0; <m1^c> = <m3^c> = 0.
+__global__ void k_mc_solve(Grid g, DLU lu, DBand Bs1, const double* dstar, const cd* rt, cd* m1c, cd* m2c,
+                           cd* m3c) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= (int)g.M) return;
+  const size_t M = g.M;
+  const int ny = g.ny;
+  if (is_nyquist(g, m)) {
+    for (int i = 0; i <= ny; ++i) m2c[(size_t)i * M + m] = mk(0, 0);
+    for (int i = 0; i < ny; ++i) m1c[(size_t)i * M + m] = m3c[(size_t)i * M + m] = mk(0, 0);
+    return;
+  }
+  if (m == 0) {
+    cd c = mk(0, 0);
+    m2c[(size_t)ny * M] = c;
+    for (int i = ny - 1; i >= 0; --i) {
+      c = c + (1.0 / __ldg(dstar + i)) * rt[(size_t)i * M];
+      m2c[(size_t)i * M] = c;
+      m1c[(size_t)i * M] = m3c[(size_t)i * M] = mk(0, 0);
+    }
+    return;
+  }
+  double k1, k3;
+  wavenumbers(g, m, k1, k3);
+  const double k = sqrt(k1 * k1 + k3 * k3), ik = 1.0 / k;
+  band_solve(
+      lu, m, m2c, M,
+      [&](int i) {
+        if (i == 0 || i == ny) return mk(0, 0);
+        const cd d = band_row(Bs1, i, rt, M, m);
+        return mk(-d.re, -d.im);
+      },
+      [&](int i, cd x, cd xnext) {
+        m2c[(size_t)i * M + m] = x;
+        if (i < ny) {
+          const cd dm = __ldg(dstar + i) * (xnext - x);
+          const cd mpar = ik * times_i(rt[(size_t)i * M + m] + dm);
+          m1c[(size_t)i * M + m] = (k1 * ik) * mpar;
+          m3c[(size_t)i * M + m] = (k3 * ik) * mpar;
+        }
+      });
+}
+
+// ------------------------------------------------------------------ RHS streams (Eq. DNS_system)
+// sv[0..9] = C11, C12, C13, C22, C23, C33, u1, u2, u3, rho at the Greville points (values).
+// With H_i = d_j C_ij + mu lap u_i - g rho delta_i2 (the (1/3) grad div u part of the viscous force is
+// a gradient and cancels in both curls):
+//   RHS_Omega2 = i k3 H1 - i k1 H3 = st0 + d/dy st1 + d2/dy2 st2,
+//   RHS_phi2 = -k^2 H2 - d/dy (i k1 H1 + i k3 H3) = st3 + d/dy st4 + d2/dy2 st5 + d3/dy3 st6,
+// so only st1..st6 need B-spline coefficients (st0 is already the value at g).
+// k = 0: st1 = <C12>, st2 = mu <u1>, st4 = <C23>, st5 = mu <u3> carry the mean equations
+// (Eq. mean_m1m3); the k = 0 values of all seven streams vanish otherwise.
+__global__ void k_rhs_combine(Grid g, double mu, double grav, Fields10C sv, Fields7 st) {
+  const size_t n = (size_t)g.ny * g.M;
+  for (size_t o = blockIdx.x * (size_t)blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x) {
+    const int m = (int)(o % g.M);
+    cd r[7];
+    for (int q = 0; q < 7; ++q) r[q] = mk(0, 0);
+    if (!is_nyquist(g, m)) {
+      const cd C11 = sv.p[0][o], C12 = sv.p[1][o], C13 = sv.p[2][o], C22 = sv.p[3][o], C23 = sv.p[4][o],
+               C33 = sv.p[5][o], u1 = sv.p[6][o], u2 = sv.p[7][o], u3 = sv.p[8][o], rho = sv.p[9][o];
+      if (m == 0) {
+        r[1] = C12;
+        r[2] = mu * u1;
+        r[4] = C23;
+        r[5] = mu * u3;
+      } else {
+        double k1, k3;
+        wavenumbers(g, m, k1, k3);
+        const double k2 = k1 * k1 + k3 * k3;
+        const cd w13 = times_i(k3 * u1 - k1 * u3);        // i k3 u1 - i k1 u3
+        const cd d13 = times_i(k1 * u1 + k3 * u3);        // i k1 u1 + i k3 u3
+        const cd c1223 = times_i(k1 * C12 + k3 * C23);    // i k1 C12 + i k3 C23
+        r[0] = (-k1 * k3) * C11 + (k1 * k1 - k3 * k3) * C13 + (k1 * k3) * C33 - (mu * k2) * w13;
+        r[1] = times_i(k3 * C12 - k1 * C23);
+        r[2] = mu * w13;
+        r[3] = (-k2) * (c1223 - grav * rho) + (mu * k2 * k2) * u2;
+        r[4] = (-k2) * C22 + (k1 * k1) * C11 + (2.0 * k1 * k3) * C13 + (k3 * k3) * C33 + (mu * k2) * d13;
+        r[5] = mk(-c1223.re, -c1223.im) - (mu * k2) * u2;
+        r[6] = (-mu) * d13;
+      }
+    }
+    for (int q = 0; q < 7; ++q) st.p[q][o] = r[q];
+  }
+}
+
+// RHS values from the streams (st1..st6 now B coefficients): R_Omega2 at g (ny rows), R_phi2 at g*
+// (ny + 1 rows), and for k = 0 the mean RHS (2 ny reals).
+__global__ void k_rhs_eval(Grid g, DBand B1g, DBand B2g, DBand Bs0, DBand Bs1, DBand Bs2, DBand Bs3, Fields7C st,
+                           cd* r_om, cd* r_phi, double* r_m) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= (int)g.M) return;
+  const size_t M = g.M;
+  const int ny = g.ny;
+  if (m == 0 || is_nyquist(g, m)) {
+    for (int i = 0; i < ny; ++i) r_om[(size_t)i * M + m] = mk(0, 0);
+    for (int i = 0; i <= ny; ++i) r_phi[(size_t)i * M + m] = mk(0, 0);
+    if (m == 0)
+      for (int i = 0; i < ny; ++i) {
+        r_m[i] = (band_row(B1g, i, st.p[1], M, 0) + band_row(B2g, i, st.p[2], M, 0)).re;
+        r_m[ny + i] = (band_row(B1g, i, st.p[4], M, 0) + band_row(B2g, i, st.p[5], M, 0)).re;
+      }
+    return;
+  }
+  for (int i = 0; i < ny; ++i)
+    r_om[(size_t)i * M + m] = st.p[0][(size_t)i * M + m] + band_row(B1g, i, st.p[1], M, m) + band_row(B2g, i, st.p[2], M, m);
+  for (int i = 0; i <= ny; ++i)
+    r_phi[(size_t)i * M + m] = band_row(Bs0, i, st.p[3], M, m) + band_row(Bs1, i, st.p[4], M, m) +
+                               band_row(Bs2, i, st.p[5], M, m) + band_row(Bs3, i, st.p[6], M, m);
+}
+
+// ------------------------------------------------------------------ RK2 update (step 6)
+// Midpoint RK2 in low-storage form at the collocation points, X^{s+1} = X^s + dt (al R^s + be R^{s-1}),
+// followed by the wall-row solves. Omega2 (job 0): values at g, Dirichlet rows (interpolation LU);
+// z (job 1): values at g advanced with (dz/dt)^{k_f}, Neumann rows dz/dy(+-1) = 0 (Neumann LU).
+__global__ void k_update_om_z(Grid g, DBand B0g, DLU lu_i, DLU lu_n, UpdateArgs a) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= (int)g.M) return;
+  const size_t M = g.M;
+  const int ny = g.ny;
+  const int job = blockIdx.y;
+  cd* out = job == 0 ? a.om_new : a.z_new;
+  if (is_nyquist(g, m) || (job == 0 && m == 0)) {
+    for (int i = 0; i < ny; ++i) out[(size_t)i * M + m] = mk(0, 0);
+    return;
+  }
+  const double dt = a.dt, al = a.al, be = a.be;
+  if (job == 0) {
+    band_solve(
+        lu_i, m, out, M,
+        [&](int i) {
+          if (i == 0 || i == ny - 1) return mk(0, 0);
+          const size_t o = (size_t)i * M + m;
+          return band_row(B0g, i, a.om, M, m) + dt * (al * a.r_om[o] + be * a.r_om_prev[o]);
+        },
+        [&](int i, cd x, cd) { out[(size_t)i * M + m] = x; });
+  } else {
+    band_solve(
+        lu_n, m, out, M,
+        [&](int i) {
+          if (i == 0 || i == ny - 1) return mk(0, 0);
+          const int c = B0g.c0[i];
+          const double* v = B0g.v + (size_t)i * B0g.w;
+          cd acc = mk(0, 0);
+          for (int q = 0; q < B0g.w; ++q) {
+            const size_t o = (size_t)(c + q) * M + m;
+            const cd zz = a.z[o] + dt * (al * a.zdot[o] + be * a.zdot_prev[o]);
+            acc = fma_rc(__ldg(v + q), zz, acc);
+          }
+          return acc;
+        },
+        [&](int i, cd x, cd) { out[(size_t)i * M + m] = x; });
+  }
+}
+
+// Plane means <m1>, <m3>: values at g advanced, no-slip Dirichlet rows (one thread per component).
+__global__ void k_update_means(Grid g, DBand B0g, DLU lu_i, UpdateArgs a) {
+  const int c = threadIdx.x;
+  if (c > 1) return;
+  const int ny = g.ny;
+  const double* cur = c == 0 ? a.mm1 : a.mm3;
+  double* out = c == 0 ? a.mm1_new : a.mm3_new;
+  const double* r = a.r_m + c * ny;
+  const double* rp = a.r_m_prev + c * ny;
+  // real solve through the complex routine with a 1-mode stride
+  double win[KMAX];
+  for (int q = 0; q < KMAX; ++q) win[q] = 0.0;
+  for (int i = 0; i < ny; ++i) {
+    double v = 0.0;
+    if (i > 0 && i < ny - 1) v = band_row_real(B0g, i, cur) + a.dt * (a.al * r[i] + a.be * rp[i]);
+    const int nl = lu_i.nl[i];
+    for (int q = 1; q <= nl; ++q) v -= lu_i.lo[i * lu_i.K + q - 1] * win[q - 1];
+    for (int q = KMAX - 1; q > 0; --q) win[q] = win[q - 1];
+    win[0] = v;
+    out[i] = v;
+  }
+  for (int q = 0; q < KMAX; ++q) win[q] = 0.0;
+  for (int i = ny - 1; i >= 0; --i) {
+    double v = out[i];
+    const int nu = lu_i.nu[i];
+    for (int q = 1; q <= nu; ++q) v -= lu_i.up[i * lu_i.K + q - 1] * win[q - 1];
+    v *= lu_i.invd[i];
+    for (int q = KMAX - 1; q > 0; --q) win[q] = win[q - 1];
+    win[0] = v;
+    out[i] = v;
+  }
+}
+
+// m2^d (Eq. phi_poisson): phi2 = (B*'' - k^2 B*) m2^d at g*_2 .. g*_{ny-2} advanced with RHS_phi2,
+// four no-slip rows m2^d(+-1) = dm2^d/dy(+-1) = 0; per-mode LU. k = 0: m2^d = 0.
+__global__ void k_update_m2(Grid g, DBand Ss0, DBand Ss2, DLU lu, UpdateArgs a) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= (int)g.M) return;
+  const size_t M = g.M;
+  const int ny = g.ny;
+  cd* out = a.m2_new;
+  if (m == 0 || is_nyquist(g, m)) {
+    for (int i = 0; i <= ny; ++i) out[(size_t)i * M + m] = mk(0, 0);
+    return;
+  }
+  double k1, k3;
+  wavenumbers(g, m, k1, k3);
+  const double k2 = k1 * k1 + k3 * k3;
+  const double dt = a.dt, al = a.al, be = a.be;
+  band_solve(
+      lu, m, out, M,
+      [&](int i) {
+        if (i < 2 || i > ny - 2) return mk(0, 0);
+        const size_t o = (size_t)i * M + m;
+        const cd phi = band_row(Ss2, i, a.m2, M, m) - k2 * band_row(Ss0, i, a.m2, M, m);
+        return phi + dt * (al * a.r_phi[o] + be * a.r_phi_prev[o]);
+      },
+      [&](int i, cd x, cd) { out[(size_t)i * M + m] = x; });
+}
+
+// ------------------------------------------------------------------ elementwise helpers
+// BDF-like guess (Eq. dzdt_guesses): zdot = (a0 z^s + a1 z^{s-1} + a2 z^{s-2} + a3 z^{s-3}) / dt.
+__global__ void k_bdf(size_t n, double a0, double a1, double a2, double a3, double idt, const cd* z, const cd* h0,
+                      const cd* h1, const cd* h2, cd* out) {
+  for (size_t o = blockIdx.x * (size_t)blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x)
+    out[o] = idt * (a0 * z[o] + a1 * h0[o] + a2 * h1[o] + a3 * h2[o]);
+}
+
+// start-up history: zh_q = z - c_q dt zdot
+__global__ void k_backfill(size_t n, double c0, double c1, double c2, const cd* z, const cd* zdot, cd* h0, cd* h1,
+                           cd* h2) {
+  for (size_t o = blockIdx.x * (size_t)blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x) {
+    const cd zz = z[o], d = zdot[o];
+    h0[o] = zz - c0 * d;
+    h1[o] = zz - c1 * d;
+    h2[o] = zz - c2 * d;
+  }
+}
+
+// zero the Nyquist slots of a spectral field and, if zero_mean, its k = 0 slot
+__global__ void k_sanitize(Grid g, int rows, cd* f, int zero_mean) {
+  const size_t n = (size_t)rows * g.M;
+  for (size_t o = blockIdx.x * (size_t)blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x) {
+    const int m = (int)(o % g.M);
+    if (is_nyquist(g, m) || (zero_mean && m == 0)) f[o] = mk(0, 0);
+  }
+}
+
+// ------------------------------------------------------------------ per-mode factorisation
+// LU (no pivoting) of A(k^2) = A2 - k^2 A0 for every mode with k != 0; A2, A0 in diagonal band storage
+// (half-width K, shared), profile nl/nu shared; factors stored per mode (stride M).
+__global__ void k_factor(Grid g, int n, int K, const double* A2, const double* A0, const int* nl, const int* nu,
+                         double* lo, double* up, double* invd) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= (int)g.M) return;
+  const size_t M = g.M;
+  const int W = 2 * K + 1;
+  if (m == 0 || is_nyquist(g, m)) {
+    for (int i = 0; i < n; ++i) {
+      for (int q = 0; q < K; ++q) lo[(size_t)(i * K + q) * M + m] = up[(size_t)(i * K + q) * M + m] = 0.0;
+      invd[(size_t)i * M + m] = 1.0;
+    }
+    return;
+  }
+  double k1, k3;
+  wavenumbers(g, m, k1, k3);
+  const double k2 = k1 * k1 + k3 * k3;
+  double row[2 * KMAX + 1];
+  for (int i = 0; i < n; ++i) {
+    for (int q = 0; q < W; ++q) row[q] = A2[(size_t)i * W + q] - k2 * A0[(size_t)i * W + q];
+    for (int q = nl[i]; q >= 1; --q) {
+      const int c = i - q;
+      const double l = row[K - q] * invd[(size_t)c * M + m];
+      lo[(size_t)(i * K + q - 1) * M + m] = l;
+      row[K - q] = 0.0;
+      for (int r = 1; r <= nu[c]; ++r) row[K - q + r] -= l * up[(size_t)(c * K + r - 1) * M + m];
+    }
+    invd[(size_t)i * M + m] = 1.0 / row[K];
+    for (int r = 1; r <= K; ++r) up[(size_t)(i * K + r - 1) * M + m] = r <= nu[i] ? row[K + r] : 0.0;
+    for (int q = nl[i] + 1; q <= K; ++q) lo[(size_t)(i * K + q - 1) * M + m] = 0.0;
+  }
+}
+
+}  // namespace lmvd

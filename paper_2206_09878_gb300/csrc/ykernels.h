@@ -1,0 +1,80 @@
+// Declarations of the y-direction and elementwise kernels (see ykernels.cu, pointwise.cu).
+#pragma once
+#include "lmvd_internal.h"
+
+namespace lmvd {
+
+struct Fields8 {
+  cd* p[8];
+};
+struct Fields7 {
+  cd* p[7];
+};
+struct Fields7C {
+  const cd* p[7];
+};
+struct Fields10C {
+  const cd* p[10];
+};
+struct EvalJob {
+  DBand B;
+  const cd* in;
+  cd* out;
+};
+struct EvalJobs {
+  EvalJob j[4];
+};
+struct SolveJob {
+  const cd* in;
+  const cd* add;  // may be null
+  cd* out;
+};
+struct SolveJobs {
+  SolveJob j[8];
+};
+struct UpdateArgs {
+  double dt, al, be;
+  const cd *om, *r_om, *r_om_prev, *z, *zdot, *zdot_prev, *m2, *r_phi, *r_phi_prev;
+  const double *mm1, *mm3, *r_m, *r_m_prev;
+  cd *om_new, *z_new, *m2_new;
+  double *mm1_new, *mm3_new;
+};
+
+__global__ void k_eval_p1(Grid g, DBand B0g, DBand B1g, DBand B2g, DBand Sg0, DBand Sg1, const cd* z,
+                          const cd* om, const cd* m2, const double* mm1, const double* mm3, Fields8 out);
+__global__ void k_eval(Grid g, EvalJobs jobs);
+__global__ void k_solve_shared(Grid g, DLU lu, SolveJobs jobs);
+__global__ void k_mc_solve(Grid g, DLU lu, DBand Bs1, const double* dstar, const cd* rt, cd* m1c, cd* m2c,
+                           cd* m3c);
+__global__ void k_rhs_combine(Grid g, double mu, double grav, Fields10C sv, Fields7 st);
+__global__ void k_rhs_eval(Grid g, DBand B1g, DBand B2g, DBand Bs0, DBand Bs1, DBand Bs2, DBand Bs3, Fields7C st,
+                           cd* r_om, cd* r_phi, double* r_m);
+__global__ void k_update_om_z(Grid g, DBand B0g, DLU lu_i, DLU lu_n, UpdateArgs a);
+__global__ void k_update_means(Grid g, DBand B0g, DLU lu_i, UpdateArgs a);
+__global__ void k_update_m2(Grid g, DBand Ss0, DBand Ss2, DLU lu, UpdateArgs a);
+__global__ void k_bdf(size_t n, double a0, double a1, double a2, double a3, double idt, const cd* z, const cd* h0,
+                      const cd* h1, const cd* h2, cd* out);
+__global__ void k_backfill(size_t n, double c0, double c1, double c2, const cd* z, const cd* zdot, cd* h0, cd* h1,
+                           cd* h2);
+__global__ void k_sanitize(Grid g, int rows, cd* f, int zero_mean);
+__global__ void k_factor(Grid g, int n, int K, const double* A2, const double* A0, const int* nl, const int* nu,
+                         double* lo, double* up, double* invd);
+
+// pointwise.cu: physical-space products (Sec. 2.1, 4.3, 5)
+struct EosArgs {
+  double rh, rl, kappa;
+};
+__global__ void k_products_p1(size_t n, EosArgs e, const double* zp, const double* zx, const double* zz,
+                              const double* zy, const double* lapz, const double* m1, const double* m2,
+                              const double* m3, double* rho, double* invrho, double* fprime, double* w1, double* w2,
+                              double* w3, double* rz);
+__global__ void k_product_rt(size_t n, const double* fprime, const double* zdot, double* out);
+__global__ void k_product_L(size_t n, const double* w1, const double* w2, const double* w3, const double* m1,
+                            const double* m2, const double* m3, double* out);
+struct P2Out {
+  double* p[10];
+};
+__global__ void k_products_p2(size_t n, const double* md1, const double* md2, const double* md3, const double* mc1,
+                              const double* mc2, const double* mc3, const double* rho, const double* invrho, P2Out o);
+
+}  // namespace lmvd

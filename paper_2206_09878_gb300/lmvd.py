@@ -1,0 +1,224 @@
+"""Thin Python binding of liblmvd (include/lmvd.h): argument marshalling only.
+
+Every function has the name of the C entry point it calls. Array arguments are torch tensors
+(CUDA device memory, or host memory -- pinned for asynchronous copies) with the layouts of
+lmvd.h: complex128 [y][kz][kx] spectral arrays, float64 plane means. No computation happens
+here; if the compiled library is missing this module raises ImportError instead of falling back.
+"""
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblmvd.so")
+
+LMVD_FIELD_RZ = 0
+LMVD_FIELD_ZDOT = 1
+LMVD_FIELD_RHO_T = 2
+LMVD_FIELD_MC1 = 3
+LMVD_FIELD_MC2 = 4
+LMVD_FIELD_MC3 = 5
+LMVD_FIELD_R_OMEGA2 = 6
+LMVD_FIELD_R_PHI2 = 7
+LMVD_FIELD_R_MEANS = 8
+
+
+class lmvd_config(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("spline_order", ctypes.c_int),
+                ("lx", ctypes.c_double), ("lz", ctypes.c_double), ("y0", ctypes.c_double), ("y1", ctypes.c_double),
+                ("re", ctypes.c_double), ("sc", ctypes.c_double), ("fr", ctypes.c_double),
+                ("rho_heavy", ctypes.c_double), ("rho_light", ctypes.c_double),
+                ("dt", ctypes.c_double), ("kf", ctypes.c_int), ("beta_n", ctypes.c_double),
+                ("beta_p", ctypes.c_double), ("n_startup", ctypes.c_int)]
+
+
+class LmvdError(RuntimeError):
+    def __init__(self, code, where):
+        super().__init__("%s failed: %s (%d)" % (where, lmvd_strerror(code), code))
+        self.code = code
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("liblmvd.so is not built (%s); run paper_2206_09878_gb300.build.build()" % LIB_PATH)
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I, D, S = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+    sig = {
+        "lmvd_default_config": (I, [ctypes.POINTER(lmvd_config), I, I, I]),
+        "lmvd_create": (I, [ctypes.POINTER(lmvd_config), P, ctypes.POINTER(P)]),
+        "lmvd_destroy": (None, [P]),
+        "lmvd_set_state": (I, [P, P, P, P, P, P, P]),
+        "lmvd_get_state": (I, [P, P, P, P, P, P, P]),
+        "lmvd_history_bytes": (S, [P]),
+        "lmvd_advance_substage": (I, [P]),
+        "lmvd_step": (I, [P, I]),
+        "lmvd_get_field": (I, [P, I, P]),
+        "lmvd_field_bytes": (S, [P, I]),
+        "lmvd_substage_index": (I, [P]),
+        "lmvd_synchronize": (I, [P]),
+        "lmvd_status": (I, [P]),
+        "lmvd_strerror": (ctypes.c_char_p, [I]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _ = D
+    return lib
+
+
+_lib = _load()
+
+EXPORTED = ("lmvd_default_config", "lmvd_create", "lmvd_destroy", "lmvd_set_state", "lmvd_get_state",
+            "lmvd_history_bytes", "lmvd_advance_substage", "lmvd_step", "lmvd_get_field", "lmvd_field_bytes",
+            "lmvd_substage_index", "lmvd_synchronize", "lmvd_status", "lmvd_strerror")
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_contiguous():
+        raise ValueError("arrays passed to liblmvd must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _check(code, where):
+    if code != 0:
+        raise LmvdError(code, where)
+    return code
+
+
+def lmvd_strerror(code):
+    return _lib.lmvd_strerror(int(code)).decode()
+
+
+def lmvd_default_config(nx, ny, nz, **overrides):
+    cfg = lmvd_config()
+    _check(_lib.lmvd_default_config(ctypes.byref(cfg), nx, ny, nz), "lmvd_default_config")
+    for k, v in overrides.items():
+        if not hasattr(cfg, k):
+            raise KeyError(k)
+        setattr(cfg, k, v)
+    return cfg
+
+
+def lmvd_create(cfg, stream=None):
+    """Returns an opaque context handle (ctypes.c_void_p). stream: torch.cuda.Stream or None (current)."""
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    h = ctypes.c_void_p()
+    _check(_lib.lmvd_create(ctypes.byref(cfg), ctypes.c_void_p(stream.cuda_stream), ctypes.byref(h)), "lmvd_create")
+    return h
+
+
+def lmvd_destroy(h):
+    _lib.lmvd_destroy(h)
+
+
+def lmvd_set_state(h, z, om, m2, mm1, mm3, history=None):
+    _check(_lib.lmvd_set_state(h, _ptr(z), _ptr(om), _ptr(m2), _ptr(mm1), _ptr(mm3), _ptr(history)),
+           "lmvd_set_state")
+
+
+def lmvd_get_state(h, z=None, om=None, m2=None, mm1=None, mm3=None, history=None):
+    _check(_lib.lmvd_get_state(h, _ptr(z), _ptr(om), _ptr(m2), _ptr(mm1), _ptr(mm3), _ptr(history)),
+           "lmvd_get_state")
+
+
+def lmvd_history_bytes(h):
+    return int(_lib.lmvd_history_bytes(h))
+
+
+def lmvd_advance_substage(h):
+    _check(_lib.lmvd_advance_substage(h), "lmvd_advance_substage")
+
+
+def lmvd_step(h, nsteps):
+    _check(_lib.lmvd_step(h, int(nsteps)), "lmvd_step")
+
+
+def lmvd_field_bytes(h, which):
+    return int(_lib.lmvd_field_bytes(h, int(which)))
+
+
+def lmvd_get_field(h, which, out):
+    _check(_lib.lmvd_get_field(h, int(which), _ptr(out)), "lmvd_get_field")
+
+
+def lmvd_substage_index(h):
+    return int(_lib.lmvd_substage_index(h))
+
+
+def lmvd_synchronize(h):
+    _check(_lib.lmvd_synchronize(h), "lmvd_synchronize")
+
+
+def lmvd_status(h):
+    return int(_lib.lmvd_status(h))
+
+
+# ---------------------------------------------------------------- convenience (still marshalling only)
+class Context:
+    """Owns one lmvd context plus torch buffers shaped for its state; frees the context on close()."""
+
+    def __init__(self, cfg, device="cuda", stream=None):
+        self.cfg = cfg
+        self.device = torch.device(device)
+        self.h = lmvd_create(cfg, stream)
+        nxh = cfg.nx // 2 + 1
+        self.shape = (cfg.ny, cfg.nz, nxh)
+        self.shape_m2 = (cfg.ny + 1, cfg.nz, nxh)
+
+    def empty_state(self, device=None, pin=False):
+        dev = self.device if device is None else torch.device(device)
+        kw = dict(device=dev)
+        if pin and dev.type == "cpu":
+            kw["pin_memory"] = True
+        return dict(z=torch.zeros(self.shape, dtype=torch.complex128, **kw),
+                    om=torch.zeros(self.shape, dtype=torch.complex128, **kw),
+                    m2=torch.zeros(self.shape_m2, dtype=torch.complex128, **kw),
+                    mm1=torch.zeros(self.cfg.ny, dtype=torch.float64, **kw),
+                    mm3=torch.zeros(self.cfg.ny, dtype=torch.float64, **kw))
+
+    def set_state(self, st, history=None):
+        lmvd_set_state(self.h, st["z"], st["om"], st["m2"], st["mm1"], st["mm3"], history)
+
+    def get_state(self, out=None, history=None):
+        out = self.empty_state() if out is None else out
+        lmvd_get_state(self.h, out["z"], out["om"], out["m2"], out["mm1"], out["mm3"], history)
+        return out
+
+    def history_buffer(self, device=None):
+        dev = self.device if device is None else torch.device(device)
+        return torch.zeros(lmvd_history_bytes(self.h), dtype=torch.uint8, device=dev)
+
+    def field(self, which):
+        nbytes = lmvd_field_bytes(self.h, which)
+        if which == LMVD_FIELD_R_MEANS:
+            out = torch.zeros(nbytes // 8, dtype=torch.float64, device=self.device)
+        else:
+            rows = nbytes // (16 * self.cfg.nz * (self.cfg.nx // 2 + 1))
+            out = torch.zeros((rows, self.cfg.nz, self.cfg.nx // 2 + 1), dtype=torch.complex128, device=self.device)
+        lmvd_get_field(self.h, which, out)
+        return out
+
+    def advance_substage(self):
+        lmvd_advance_substage(self.h)
+
+    def step(self, n):
+        lmvd_step(self.h, n)
+
+    def synchronize(self):
+        lmvd_synchronize(self.h)
+
+    def close(self):
+        if self.h is not None:
+            lmvd_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

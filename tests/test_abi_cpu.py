@@ -1,0 +1,57 @@
+"""CPU checks of the C-ABI library: it loads, exports every entry point of include/lmvd.h, and its
+host-side argument validation rejects bad configurations before any CUDA work."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2206_09878_gb300 import build
+    if not os.path.exists(build.LIB):
+        build.build()
+    from paper_2206_09878_gb300 import lmvd
+    return lmvd
+
+
+def declared():
+    src = open(os.path.join(ROOT, "include", "lmvd.h")).read()
+    return sorted(set(re.findall(r"\b(lmvd_[a-z_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", lib.LIB_PATH], capture_output=True, text=True).stdout
+    syms = {l.split()[-1] for l in out.splitlines()}
+    missing = [s for s in declared() if s not in syms]
+    assert not missing, missing
+    assert set(declared()) == set(lib.EXPORTED)
+
+
+def test_config_struct_layout_matches(lib):
+    cfg = lib.lmvd_default_config(32, 33, 32)
+    assert ctypes.sizeof(cfg) == 128
+    assert (cfg.spline_order, cfg.kf, cfg.n_startup) == (6, 4, 20)
+    assert cfg.beta_n == 0.0 and cfg.beta_p == -4.0 and abs(cfg.rho_light - 1 / 3) < 1e-16
+
+
+@pytest.mark.parametrize("bad", [dict(nx=7), dict(ny=5), dict(spline_order=3), dict(dt=0.0), dict(re=-1.0),
+                                 dict(y1=-2.0), dict(kf=-1)])
+def test_invalid_configs_rejected_without_gpu(lib, bad):
+    cfg = lib.lmvd_default_config(32, 33, 32)
+    for k, v in bad.items():
+        setattr(cfg, k, v)
+    h = ctypes.c_void_p()
+    rc = lib._lib.lmvd_create(ctypes.byref(cfg), None, ctypes.byref(h))
+    assert rc == -1 and not h.value
+
+
+def test_null_arguments(lib):
+    assert lib._lib.lmvd_create(None, None, None) == -1
+    assert lib._lib.lmvd_advance_substage(None) == -1
+    assert lib._lib.lmvd_history_bytes(None) == 0
+    assert lib.lmvd_strerror(-3) == "device out of memory"
