@@ -138,6 +138,24 @@ int lmvd_synchronize(lmvd_ctx* ctx);
 /* First error latched in the context (LMVD_OK if none). */
 int lmvd_status(const lmvd_ctx* ctx);
 
+/* Kernel accounting (no paper counterpart: observability of this implementation).
+ * Every kernel the context enqueues belongs to one of LMVD_KERNEL_CLASSES classes
+ * (lmvd_kernel_class_name: fft_z_inverse, fft_x_inverse, fft_x_forward, fft_z_forward, eval_pass1,
+ * eval, solve_collocation, solve_mc, rhs_combine, rhs_eval, rk_update, products, misc).
+ * lmvd_profile_enable(ctx, on): synchronizes the stream, resets the per-class counters and, when on
+ *   is non-zero, brackets every later launch with CUDA events recorded on the context's stream.
+ * lmvd_profile_read(ctx, cls, out4): synchronizes the stream and writes, for class cls since the
+ *   last enable: out4[0] total kernel milliseconds (CUDA events; 0 when profiling is off),
+ *   out4[1] launches, out4[2] algorithmic flops, out4[3] algorithmic DRAM bytes (the minimum
+ *   traffic of each launch: its inputs read once and its outputs written once).
+ * lmvd_kernel_launches(ctx): kernels enqueued since lmvd_create (-1 if ctx is NULL).
+ * Errors: INVALID_ARG (NULL ctx or out4, cls out of range), CUDA. */
+#define LMVD_KERNEL_CLASSES 13
+int lmvd_profile_enable(lmvd_ctx* ctx, int on);
+int lmvd_profile_read(lmvd_ctx* ctx, int cls, double* out4);
+const char* lmvd_kernel_class_name(int cls);
+long long lmvd_kernel_launches(const lmvd_ctx* ctx);
+
 /* Static description of an error code. */
 const char* lmvd_strerror(int code);
 

@@ -5,7 +5,7 @@ TEST INFRASTRUCTURE ONLY. Only ``tests/``, ``__graft_entry__.smoke()`` and the
 package. The product path (``paper_2206_09878_gb300``) never imports it and
 shares no code with it: the oracle has its own B-spline basis (plain
 Cox-de Boor recursion), its own banded Gaussian elimination with partial
-pivoting, and uses ``numpy.fft`` as the transform primitive.
+pivoting, and uses ``scipy.fft`` (pocketfft) as the transform primitive.
 
 Modules
 -------

@@ -10,9 +10,14 @@ Physical arrays have shape (ny, pz, px) with px = 3 nx / 2, pz = 3 nz / 2: the
 padded grid on which products are formed (3/2-rule dealiasing).
 Normalisation: f(x, z) = sum_k fhat_k exp(i k.x) (unscaled synthesis), so the
 analysis carries 1 / (px pz).
-numpy.fft is the transform primitive.
+scipy.fft (pocketfft) is the transform primitive, run with one worker per host core.
 """
+import os
+
 import numpy as np
+import scipy.fft as sfft
+
+WORKERS = os.cpu_count() or 1
 
 
 def padded_shape(nx, nz):
@@ -29,14 +34,14 @@ def to_phys(fhat, nx, nz):
     h = nz // 2
     w[:, :h, :nx // 2] = fhat[:, :h, :nx // 2]                   # kz = 0 .. nz/2 - 1
     w[:, pz - h + 1:, :nx // 2] = fhat[:, h + 1:, :nx // 2]      # kz = -nz/2 + 1 .. -1
-    return np.fft.irfft2(w, s=(pz, px), axes=(1, 2), norm="forward")
+    return sfft.irfft2(w, s=(pz, px), axes=(1, 2), norm="forward", workers=WORKERS)
 
 
 def to_spec(f, nx, nz):
     """Physical (ny, pz, px) -> spectral (ny, nz, nx/2+1), truncated, Nyquist zero."""
     px, pz = padded_shape(nx, nz)
     assert f.shape[1:] == (pz, px)
-    w = np.fft.rfft2(f, axes=(1, 2), norm="forward")
+    w = sfft.rfft2(f, axes=(1, 2), norm="forward", workers=WORKERS)
     out = np.zeros((f.shape[0], nz, nx // 2 + 1), dtype=np.complex128)
     h = nz // 2
     out[:, :h, :nx // 2] = w[:, :h, :nx // 2]

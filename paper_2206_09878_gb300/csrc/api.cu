@@ -18,7 +18,53 @@ struct lmvd_ctx {
   long long s_blob = 0;
 };
 
+namespace lmvd {
+
+cudaEvent_t prof_begin(Ctx& c) {
+  c.prof.launches++;
+  if (!c.prof.on) return nullptr;
+  cudaEvent_t a;
+  if (!c.prof.pool.empty()) {
+    a = c.prof.pool.back();
+    c.prof.pool.pop_back();
+  } else if (cudaEventCreate(&a) != cudaSuccess) {
+    return nullptr;
+  }
+  cudaEventRecord(a, c.stream);
+  return a;
+}
+
+void prof_end(Ctx& c, int cls, cudaEvent_t a, double flops, double bytes) {
+  c.prof.n[cls]++;
+  c.prof.flops[cls] += flops;
+  c.prof.bytes[cls] += bytes;
+  if (!a) return;
+  cudaEvent_t b;
+  if (!c.prof.pool.empty()) {
+    b = c.prof.pool.back();
+    c.prof.pool.pop_back();
+  } else if (cudaEventCreate(&b) != cudaSuccess) {
+    c.prof.pool.push_back(a);
+    return;
+  }
+  cudaEventRecord(b, c.stream);
+  c.prof.pending.push_back(Prof::Pending{cls, a, b});
+}
+
+}  // namespace lmvd
+
 namespace {
+
+// fold recorded event pairs into per-class milliseconds (the stream must be synchronised)
+void prof_collect(Ctx& c) {
+  for (auto& p : c.prof.pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) c.prof.ms[p.cls] += ms;
+    c.prof.pool.push_back(p.a);
+    c.prof.pool.push_back(p.b);
+  }
+  c.prof.pending.clear();
+}
 
 constexpr int TPB_MODE = 128;
 
@@ -78,7 +124,8 @@ int upload_lu(Ctx& c, const BandLU& f, DLU& d) {
   if (!e) e = upload(c, f.nl, &nl);
   if (!e) e = upload(c, f.nu, &nu);
   if (e) return e;
-  d = DLU{lo, up, invd, nl, nu, f.n, f.K, 0};
+  d = DLU{lo, up, invd, nl, nu, f.n, f.K, 0, 0.0};
+  for (int i = 0; i < f.n; ++i) d.flops_per_mode += 4.0 * (f.nl[i] + f.nu[i]) + 2.0;
   return LMVD_OK;
 }
 
@@ -147,8 +194,10 @@ int factor_per_mode(Ctx& c, const PerMode& pm, int K, DLU& out) {
   c.small_allocs.push_back(up);
   if (cudaMalloc(&invd, sizeof(double) * (size_t)n * M) != cudaSuccess) return LMVD_ERR_OOM;
   c.small_allocs.push_back(invd);
-  k_factor<<<mode_blocks(c.g), TPB_MODE, 0, c.stream>>>(c.g, n, K, A2, A0, dnl, dnu, lo, up, invd);
-  out = DLU{lo, up, invd, dnl, dnu, n, K, M};
+  LMVD_LAUNCH(c, KC_MISC, 0, 8.0 * n * (2 * K + 1) * M, k_factor, mode_blocks(c.g), TPB_MODE, 0, c.g, n, K, A2, A0,
+              dnl, dnu, lo, up, invd);
+  out = DLU{lo, up, invd, dnl, dnu, n, K, M, 0.0};
+  for (int i = 0; i < n; ++i) out.flops_per_mode += 4.0 * (nl[i] + nu[i]) + 2.0;
   return cuda_check(c);
 }
 
@@ -208,32 +257,44 @@ void carve(Ctx& c, Carver& cv) {
 void eval_jobs(Ctx& c, std::initializer_list<EvalJob> jobs) {
   EvalJobs ej{};
   int n = 0;
-  for (const EvalJob& j : jobs) ej.j[n++] = j;
-  k_eval<<<dim3(mode_blocks(c.g), n), TPB_MODE, 0, c.stream>>>(c.g, ej);
+  double rows = 0, fl = 0;
+  for (const EvalJob& j : jobs) {
+    ej.j[n++] = j;
+    rows += 2.0 * j.B.rows;
+    fl += 4.0 * j.B.rows * j.B.w;
+  }
+  LMVD_LAUNCH(c, KC_EVAL, fl * c.g.M, 16.0 * rows * c.g.M, k_eval, dim3(mode_blocks(c.g), n), TPB_MODE, 0, c.g, ej);
 }
 
 void solve_interp(Ctx& c, std::initializer_list<SolveJob> jobs, const DLU& lu) {
   SolveJobs sj{};
   int n = 0;
-  for (const SolveJob& j : jobs) sj.j[n++] = j;
-  k_solve_shared<<<dim3(mode_blocks(c.g), n), TPB_MODE, 0, c.stream>>>(c.g, lu, sj);
+  double arrays = 0;
+  for (const SolveJob& j : jobs) {
+    sj.j[n++] = j;
+    arrays += j.add ? 3 : 2;
+  }
+  const double rowsM = (double)lu.n * c.g.M;
+  LMVD_LAUNCH(c, KC_SOLVE, n * lu.flops_per_mode * c.g.M, 16.0 * arrays * rowsM, k_solve_shared,
+              dim3(mode_blocks(c.g), n), TPB_MODE, 0, c.g, lu, sj);
 }
 
 // steps 1-2: m^d and z-derived fields in physical space; rho, 1/rho, f', grad z / rho; R_z
 void physical_pass_1(Ctx& c) {
   Fields8 o{};
   for (int f = 0; f < 8; ++f) o.p[f] = c.sv[f];
-  k_eval_p1<<<mode_blocks(c.g), TPB_MODE, 0, c.stream>>>(c.g, c.B0g, c.B1g, c.B2g, c.Sg0, c.Sg1, c.z, c.om, c.m2,
-                                                         c.mm1, c.mm3, o);
+  const double SM = (double)c.g.ny * c.g.M;
+  LMVD_LAUNCH(c, KC_EVAL_P1, SM * (4.0 * 6 * c.B0g.w + 20.0), 16.0 * SM * 11 + 16.0 * c.g.M, k_eval_p1,
+              mode_blocks(c.g), TPB_MODE, 0, c.g, c.B0g, c.B1g, c.B2g, c.Sg0, c.Sg1, c.z, c.om, c.m2, c.mm1, c.mm3, o);
   // physical: z, zx, zz, zy, lapz -> pw[0..4]; m^d -> md[0..2]
   cd* in[8] = {c.sv[0], c.sv[1], c.sv[2], c.sv[3], c.sv[4], c.sv[5], c.sv[6], c.sv[7]};
   double* out[8] = {c.pw[0], c.pw[1], c.pw[2], c.pw[3], c.pw[4], c.md[0], c.md[1], c.md[2]};
   fft_inverse(c, in, out, 8);
   const size_t n = (size_t)c.g.ny * c.g.P;
   EosArgs e{c.cfg.rho_heavy, c.cfg.rho_light, 1.0 / (c.cfg.re * c.cfg.sc)};
-  k_products_p1<<<elem_blocks(n), 256, 0, c.stream>>>(n, e, c.pw[0], c.pw[1], c.pw[2], c.pw[3], c.pw[4], c.md[0],
-                                                      c.md[1], c.md[2], c.rho, c.invrho, c.fprime, c.w[0], c.w[1],
-                                                      c.w[2], c.pw[5]);
+  LMVD_LAUNCH(c, KC_PRODUCTS, 25.0 * n, 8.0 * 15 * n, k_products_p1, elem_blocks(n), 256, 0, n, e, c.pw[0], c.pw[1],
+              c.pw[2], c.pw[3], c.pw[4], c.md[0], c.md[1], c.md[2], c.rho, c.invrho, c.fprime, c.w[0], c.w[1],
+              c.w[2], c.pw[5]);
   double* fin[1] = {c.pw[5]};
   cd* fout[1] = {c.sv[0]};
   fft_forward(c, fin, fout, 1);
@@ -249,14 +310,19 @@ void mc_from_zdot(Ctx& c) {
     double* out[1] = {c.pw[0]};
     fft_inverse(c, in, out, 1);
   }
-  k_product_rt<<<elem_blocks(n), 256, 0, c.stream>>>(n, c.fprime, c.pw[0], c.pw[1]);
+  LMVD_LAUNCH(c, KC_PRODUCTS, 1.0 * n, 24.0 * n, k_product_rt, elem_blocks(n), 256, 0, n, c.fprime, c.pw[0], c.pw[1]);
   {
     double* in[1] = {c.pw[1]};
     cd* out[1] = {c.sv[1]};
     fft_forward(c, in, out, 1);
   }
   solve_interp(c, {SolveJob{c.sv[1], nullptr, c.rt}}, c.lu_interp);
-  k_mc_solve<<<mode_blocks(c.g), TPB_MODE, 0, c.stream>>>(c.g, c.lu_mc, c.Bs[1], c.dstar, c.rt, c.m1c, c.m2c, c.m3c);
+  {
+    const double rowsM = (double)(c.g.ny + 1) * c.g.M;
+    LMVD_LAUNCH(c, KC_MC_SOLVE, c.lu_mc.flops_per_mode * c.g.M + rowsM * (4.0 * c.Bs[1].w + 20.0),
+                rowsM * (16.0 * 4 + 8.0 * (2 * c.lu_mc.K + 1)), k_mc_solve, mode_blocks(c.g), TPB_MODE, 0, c.g,
+                c.lu_mc, c.Bs[1], c.dstar, c.rt, c.m1c, c.m2c, c.m3c);
+  }
   eval_jobs(c, {EvalJob{c.B0g, c.m1c, c.sv[0]}, EvalJob{c.Sg0, c.m2c, c.sv[1]}, EvalJob{c.B0g, c.m3c, c.sv[2]}});
   cd* in[3] = {c.sv[0], c.sv[1], c.sv[2]};
   double* out[3] = {c.pw[0], c.pw[1], c.pw[2]};
@@ -267,7 +333,8 @@ void mc_from_zdot(Ctx& c) {
 void fp_apply(Ctx& c) {
   mc_from_zdot(c);
   const size_t n = (size_t)c.g.ny * c.g.P;
-  k_product_L<<<elem_blocks(n), 256, 0, c.stream>>>(n, c.w[0], c.w[1], c.w[2], c.pw[0], c.pw[1], c.pw[2], c.pw[3]);
+  LMVD_LAUNCH(c, KC_PRODUCTS, 6.0 * n, 56.0 * n, k_product_L, elem_blocks(n), 256, 0, n, c.w[0], c.w[1], c.w[2],
+              c.pw[0], c.pw[1], c.pw[2], c.pw[3]);
   double* in[1] = {c.pw[3]};
   cd* out[1] = {c.sv[3]};
   fft_forward(c, in, out, 1);
@@ -280,7 +347,8 @@ void startup(Ctx& c) {
   cudaMemsetAsync(c.zdot, 0, sizeof(cd) * S, c.stream);
   for (int it = 0; it < c.cfg.n_startup; ++it) fp_apply(c);
   const double dt = c.cfg.dt;
-  k_backfill<<<elem_blocks(S), 256, 0, c.stream>>>(S, 0.5 * dt, dt, 1.5 * dt, c.z, c.zdot, c.zh[0], c.zh[1], c.zh[2]);
+  LMVD_LAUNCH(c, KC_MISC, 12.0 * S, 80.0 * S, k_backfill, elem_blocks(S), 256, 0, S, 0.5 * dt, dt, 1.5 * dt, c.z,
+              c.zdot, c.zh[0], c.zh[1], c.zh[2]);
   cudaMemcpyAsync(c.zdot_prev, c.zdot, sizeof(cd) * S, cudaMemcpyDeviceToDevice, c.stream);
   cudaMemsetAsync(c.r_om_prev, 0, sizeof(cd) * S, c.stream);
   cudaMemsetAsync(c.r_phi_prev, 0, sizeof(cd) * (S + c.g.M), c.stream);
@@ -304,22 +372,23 @@ int advance(Ctx& c) {
     const double b = cf.beta_p;
     a[0] = 4.0 + b; a[1] = -(5.0 + 2.0 * b); a[2] = b; a[3] = 1.0;
   }
-  k_bdf<<<elem_blocks(S), 256, 0, c.stream>>>(S, a[0], a[1], a[2], a[3], 1.0 / cf.dt, c.z, c.zh[0], c.zh[1], c.zh[2],
-                                              c.zdot);
+  LMVD_LAUNCH(c, KC_MISC, 16.0 * S, 80.0 * S, k_bdf, elem_blocks(S), 256, 0, S, a[0], a[1], a[2], a[3], 1.0 / cf.dt,
+              c.z, c.zh[0], c.zh[1], c.zh[2], c.zdot);
   // step 3
   for (int k = 0; k < cf.kf; ++k) fp_apply(c);
   mc_from_zdot(c);
   // steps 4-5: products with m = m^d + m^c, forward transforms, RHS streams, collocation solves, RHS
   P2Out q{};
   for (int f = 0; f < 10; ++f) q.p[f] = c.pw[f];
-  k_products_p2<<<elem_blocks(n), 256, 0, c.stream>>>(n, c.md[0], c.md[1], c.md[2], c.pw[0], c.pw[1], c.pw[2], c.rho,
-                                                      c.invrho, q);
+  LMVD_LAUNCH(c, KC_PRODUCTS, 18.0 * n, 8.0 * 18 * n, k_products_p2, elem_blocks(n), 256, 0, n, c.md[0], c.md[1],
+              c.md[2], c.pw[0], c.pw[1], c.pw[2], c.rho, c.invrho, q);
   fft_forward(c, c.pw, c.sv, 10);
   Fields10C svc{};
   for (int f = 0; f < 10; ++f) svc.p[f] = c.sv[f];
   Fields7 stw{};
   for (int f = 0; f < 7; ++f) stw.p[f] = c.st[f];
-  k_rhs_combine<<<elem_blocks(S), 256, 0, c.stream>>>(g, 1.0 / cf.re, 1.0 / (cf.fr * cf.fr), svc, stw);
+  LMVD_LAUNCH(c, KC_RHS_COMBINE, 90.0 * S, 16.0 * 17 * S, k_rhs_combine, elem_blocks(S), 256, 0, g, 1.0 / cf.re,
+              1.0 / (cf.fr * cf.fr), svc, stw);
   solve_interp(c,
                {SolveJob{c.st[1], nullptr, c.st[1]}, SolveJob{c.st[2], nullptr, c.st[2]},
                 SolveJob{c.st[3], nullptr, c.st[3]}, SolveJob{c.st[4], nullptr, c.st[4]},
@@ -327,8 +396,8 @@ int advance(Ctx& c) {
                c.lu_interp);
   Fields7C stc{};
   for (int f = 0; f < 7; ++f) stc.p[f] = c.st[f];
-  k_rhs_eval<<<mode_blocks(g), TPB_MODE, 0, c.stream>>>(g, c.B1g, c.B2g, c.Bs[0], c.Bs[1], c.Bs[2], c.Bs[3], stc,
-                                                        c.r_om, c.r_phi, c.r_m);
+  LMVD_LAUNCH(c, KC_RHS_EVAL, S * (4.0 * 6 * c.B1g.w + 4.0), 16.0 * 9 * S, k_rhs_eval, mode_blocks(g), TPB_MODE, 0,
+              g, c.B1g, c.B2g, c.Bs[0], c.Bs[1], c.Bs[2], c.Bs[3], stc, c.r_om, c.r_phi, c.r_m);
   // step 6: midpoint RK2, low-storage: (al, be) = (1/2, 0) at stage n, (1, -1/2) at stage '
   UpdateArgs u{};
   u.dt = cf.dt;
@@ -339,9 +408,16 @@ int advance(Ctx& c) {
   u.m2 = c.m2; u.r_phi = c.r_phi; u.r_phi_prev = c.r_phi_prev;
   u.mm1 = c.mm1; u.mm3 = c.mm3; u.r_m = c.r_m; u.r_m_prev = c.r_m_prev;
   u.om_new = c.om_new; u.z_new = c.z_new; u.m2_new = c.m2_new; u.mm1_new = c.mm1_new; u.mm3_new = c.mm3_new;
-  k_update_om_z<<<dim3(mode_blocks(g), 2), TPB_MODE, 0, c.stream>>>(g, c.B0g, c.lu_interp, c.lu_neumann, u);
-  k_update_means<<<1, 32, 0, c.stream>>>(g, c.B0g, c.lu_interp, u);
-  k_update_m2<<<mode_blocks(g), TPB_MODE, 0, c.stream>>>(g, c.Ss0, c.Ss2, c.lu_md, u);
+  LMVD_LAUNCH(c, KC_UPDATE, (c.lu_interp.flops_per_mode + c.lu_neumann.flops_per_mode) * g.M + S * (12.0 * c.B0g.w + 20.0),
+              16.0 * 8 * S, k_update_om_z,
+              dim3(mode_blocks(g), 2), TPB_MODE, 0, g, c.B0g, c.lu_interp, c.lu_neumann, u);
+  LMVD_LAUNCH(c, KC_UPDATE, 0, 0, k_update_means, 1, 32, 0, g, c.B0g, c.lu_interp, u);
+  {
+    const double Sp = (double)(g.ny + 1) * g.M;
+    LMVD_LAUNCH(c, KC_UPDATE, c.lu_md.flops_per_mode * g.M + Sp * (8.0 * c.Ss0.w + 10.0),
+                Sp * (16.0 * 4 + 8.0 * (2 * c.lu_md.K + 1)), k_update_m2, mode_blocks(g), TPB_MODE, 0, g, c.Ss0,
+                c.Ss2, c.lu_md, u);
+  }
   // history rotation (pointer swaps)
   cd* oldest = c.zh[2];
   c.zh[2] = c.zh[1];
@@ -492,6 +568,11 @@ void lmvd_destroy(lmvd_ctx* h) {
   Ctx& c = h->c;
   if (c.stream) cudaStreamSynchronize(c.stream);
   else cudaDeviceSynchronize();
+  for (auto& p : c.prof.pending) {
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  for (cudaEvent_t e : c.prof.pool) cudaEventDestroy(e);
   for (void* p : c.small_allocs) cudaFree(p);
   if (c.arena) cudaFree(c.arena);
   delete h;
@@ -515,9 +596,9 @@ int lmvd_set_state(lmvd_ctx* h, const void* z, const void* om, const void* m2, c
   if (!e) e = copy_in(c, c.mm1, mm1, R);
   if (!e) e = copy_in(c, c.mm3, mm3, R);
   if (e) return latch(c, e);
-  k_sanitize<<<elem_blocks(g.ny * g.M), 256, 0, c.stream>>>(g, g.ny, c.z, 0);
-  k_sanitize<<<elem_blocks(g.ny * g.M), 256, 0, c.stream>>>(g, g.ny, c.om, 1);
-  k_sanitize<<<elem_blocks((g.ny + 1) * g.M), 256, 0, c.stream>>>(g, g.ny + 1, c.m2, 1);
+  LMVD_LAUNCH(c, KC_MISC, 0, S, k_sanitize, elem_blocks(g.ny * g.M), 256, 0, g, g.ny, c.z, 0);
+  LMVD_LAUNCH(c, KC_MISC, 0, S, k_sanitize, elem_blocks(g.ny * g.M), 256, 0, g, g.ny, c.om, 1);
+  LMVD_LAUNCH(c, KC_MISC, 0, Sp, k_sanitize, elem_blocks((g.ny + 1) * g.M), 256, 0, g, g.ny + 1, c.m2, 1);
   if (!history) {
     startup(c);
     return cuda_check(c);
@@ -624,6 +705,38 @@ int lmvd_synchronize(lmvd_ctx* h) {
 }
 
 int lmvd_status(const lmvd_ctx* h) { return h ? h->c.status : LMVD_ERR_INVALID_ARG; }
+
+int lmvd_profile_enable(lmvd_ctx* h, int on) {
+  if (!h) return LMVD_ERR_INVALID_ARG;
+  Ctx& c = h->c;
+  if (cudaStreamSynchronize(c.stream) != cudaSuccess) return latch(c, LMVD_ERR_CUDA);
+  prof_collect(c);
+  for (int k = 0; k < KC_COUNT; ++k) c.prof.n[k] = 0, c.prof.flops[k] = c.prof.bytes[k] = c.prof.ms[k] = 0.0;
+  c.prof.on = on != 0;
+  return LMVD_OK;
+}
+
+int lmvd_profile_read(lmvd_ctx* h, int cls, double* out4) {
+  if (!h || !out4 || cls < 0 || cls >= KC_COUNT) return LMVD_ERR_INVALID_ARG;
+  Ctx& c = h->c;
+  if (cudaStreamSynchronize(c.stream) != cudaSuccess) return latch(c, LMVD_ERR_CUDA);
+  prof_collect(c);
+  out4[0] = c.prof.ms[cls];
+  out4[1] = (double)c.prof.n[cls];
+  out4[2] = c.prof.flops[cls];
+  out4[3] = c.prof.bytes[cls];
+  return LMVD_OK;
+}
+
+const char* lmvd_kernel_class_name(int cls) {
+  static const char* names[KC_COUNT] = {"fft_z_inverse", "fft_x_inverse", "fft_x_forward", "fft_z_forward",
+                                        "eval_pass1",    "eval",          "solve_collocation", "solve_mc",
+                                        "rhs_combine",   "rhs_eval",      "rk_update",     "products",
+                                        "misc"};
+  return (cls >= 0 && cls < KC_COUNT) ? names[cls] : "unknown";
+}
+
+long long lmvd_kernel_launches(const lmvd_ctx* h) { return h ? h->c.prof.launches : -1; }
 
 const char* lmvd_strerror(int code) {
   switch (code) {

@@ -257,6 +257,8 @@ int fft_prepare(Ctx& c) {
 }
 
 static inline unsigned cdiv(unsigned a, unsigned b) { return (a + b - 1) / b; }
+// conventional algorithmic flop count of one complex transform of length n: 5 n log2 n
+static inline double fft_flops(double n) { return 5.0 * n * std::log2(n); }
 
 void fft_inverse(Ctx& c, cd* const* in, double* const* out, int nf) {
   const Grid& g = c.g;
@@ -269,10 +271,13 @@ void fft_inverse(Ctx& c, cd* const* in, double* const* out, int nf) {
       fi.p[f] = in[f0 + f];
       fo.p[f] = out[f0 + f];
     }
+    const double h = g.nx / 2, ny = g.ny, pz = g.pz, px = g.px;
     dim3 gz(cdiv(g.nx / 2, c.fz.batch), g.ny, n);
-    k_fft_z_inv<<<gz, 256, smem_bytes(c.fz), c.stream>>>(c.fz, g, fi, c.tbuf, tstride);
+    LMVD_LAUNCH(c, KC_FFT_Z_INV, n * ny * h * fft_flops(pz), n * ny * h * 16.0 * ((g.nz - 1) + pz), k_fft_z_inv, gz,
+                256, smem_bytes(c.fz), c.fz, g, fi, c.tbuf, tstride);
     dim3 gx(cdiv(cdiv(g.pz, 2), c.fx.batch), g.ny, n);
-    k_fft_x_inv<<<gx, 256, smem_bytes(c.fx), c.stream>>>(c.fx, g, c.tbuf, tstride, fo);
+    LMVD_LAUNCH(c, KC_FFT_X_INV, n * ny * ((g.pz + 1) / 2) * fft_flops(px), n * ny * pz * (16.0 * h + 8.0 * px),
+                k_fft_x_inv, gx, 256, smem_bytes(c.fx), c.fx, g, c.tbuf, tstride, fo);
   }
 }
 
@@ -288,10 +293,13 @@ void fft_forward(Ctx& c, double* const* in, cd* const* out, int nf) {
       fi.p[f] = in[f0 + f];
       fo.p[f] = out[f0 + f];
     }
+    const double h = g.nx / 2, ny = g.ny, pz = g.pz, px = g.px;
     dim3 gx(cdiv(cdiv(g.pz, 2), c.fx.batch), g.ny, n);
-    k_fft_x_fwd<<<gx, 256, smem_bytes(c.fx), c.stream>>>(c.fx, g, fi, c.tbuf, tstride);
+    LMVD_LAUNCH(c, KC_FFT_X_FWD, n * ny * ((g.pz + 1) / 2) * fft_flops(px), n * ny * pz * (16.0 * h + 8.0 * px),
+                k_fft_x_fwd, gx, 256, smem_bytes(c.fx), c.fx, g, fi, c.tbuf, tstride);
     dim3 gz(cdiv(g.nx / 2 + 1, c.fz.batch), g.ny, n);
-    k_fft_z_fwd<<<gz, 256, smem_bytes(c.fz), c.stream>>>(c.fz, g, c.tbuf, tstride, fo, scale);
+    LMVD_LAUNCH(c, KC_FFT_Z_FWD, n * ny * h * fft_flops(pz), n * ny * 16.0 * (pz * h + (double)g.nz * g.nxh),
+                k_fft_z_fwd, gz, 256, smem_bytes(c.fz), c.fz, g, c.tbuf, tstride, fo, scale);
   }
 }
 

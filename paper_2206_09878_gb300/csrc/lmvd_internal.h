@@ -43,6 +43,7 @@ struct DLU {
   const int* nu;
   int n, K;
   size_t mstride;
+  double flops_per_mode;  // host-side: flops of one complex solve (sum over rows of 4 (nl + nu) + 2)
 };
 
 // Spectral field: complex [rows][nz][nxh], mode index m = jz * nxh + kx, M = nz * nxh.
@@ -79,6 +80,24 @@ struct FFTPlan {
   int radix[24];
   double2* tw = nullptr;   // tw[m] = (cos 2 pi m / n, sin 2 pi m / n), device
   int batch = 1;           // transforms per CTA
+};
+
+// ---------------------------------------------------------------- per-class launch accounting
+// Kernel classes, in the order of lmvd_kernel_class_name().
+enum KClass {
+  KC_FFT_Z_INV, KC_FFT_X_INV, KC_FFT_X_FWD, KC_FFT_Z_FWD, KC_EVAL_P1, KC_EVAL, KC_SOLVE, KC_MC_SOLVE,
+  KC_RHS_COMBINE, KC_RHS_EVAL, KC_UPDATE, KC_PRODUCTS, KC_MISC, KC_COUNT
+};
+struct Prof {
+  bool on = false;
+  long long launches = 0;       // every kernel enqueued since creation
+  long long n[KC_COUNT] = {};   // launches per class since profiling was enabled
+  double flops[KC_COUNT] = {};  // algorithmic flops per class
+  double bytes[KC_COUNT] = {};  // algorithmic DRAM bytes per class
+  double ms[KC_COUNT] = {};
+  struct Pending { int cls; cudaEvent_t a, b; };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> pool;
 };
 
 // ---------------------------------------------------------------- context
@@ -119,7 +138,19 @@ struct Ctx {
   // physical
   double *md[3], *rho, *invrho, *fprime, *w[3];
   double* pw[10];     // physical work fields
+
+  Prof prof;
 };
+
+// Bracket a launch: counts it, and with profiling on records CUDA events around it on the stream.
+cudaEvent_t prof_begin(Ctx& c);
+void prof_end(Ctx& c, int cls, cudaEvent_t a, double flops, double bytes);
+#define LMVD_LAUNCH(C, CLS, FLOPS, BYTES, KERN, GRID, BLOCK, SMEM, ...)       \
+  do {                                                                      \
+    cudaEvent_t ev_a_ = ::lmvd::prof_begin(C);                              \
+    KERN<<<GRID, BLOCK, SMEM, (C).stream>>>(__VA_ARGS__);                   \
+    ::lmvd::prof_end(C, CLS, ev_a_, (double)(FLOPS), (double)(BYTES));      \
+  } while (0)
 
 // ---------------------------------------------------------------- launchers (defined in .cu files)
 int fft_prepare(Ctx& c);                       // plans, twiddles, smem attributes

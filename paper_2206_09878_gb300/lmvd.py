@@ -59,6 +59,10 @@ def _load():
         "lmvd_synchronize": (I, [P]),
         "lmvd_status": (I, [P]),
         "lmvd_strerror": (ctypes.c_char_p, [I]),
+        "lmvd_profile_enable": (I, [P, I]),
+        "lmvd_profile_read": (I, [P, I, ctypes.POINTER(ctypes.c_double)]),
+        "lmvd_kernel_class_name": (ctypes.c_char_p, [I]),
+        "lmvd_kernel_launches": (ctypes.c_longlong, [P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -72,7 +76,9 @@ _lib = _load()
 
 EXPORTED = ("lmvd_default_config", "lmvd_create", "lmvd_destroy", "lmvd_set_state", "lmvd_get_state",
             "lmvd_history_bytes", "lmvd_advance_substage", "lmvd_step", "lmvd_get_field", "lmvd_field_bytes",
-            "lmvd_substage_index", "lmvd_synchronize", "lmvd_status", "lmvd_strerror")
+            "lmvd_substage_index", "lmvd_synchronize", "lmvd_status", "lmvd_strerror", "lmvd_profile_enable",
+            "lmvd_profile_read", "lmvd_kernel_class_name", "lmvd_kernel_launches")
+LMVD_KERNEL_CLASSES = 13
 
 
 def _ptr(t):
@@ -156,6 +162,25 @@ def lmvd_synchronize(h):
 
 def lmvd_status(h):
     return int(_lib.lmvd_status(h))
+
+
+def lmvd_profile_enable(h, on=True):
+    _check(_lib.lmvd_profile_enable(h, 1 if on else 0), "lmvd_profile_enable")
+
+
+def lmvd_profile_read(h, cls):
+    """(total_ms, launches, algorithmic_flops, algorithmic_bytes) of one kernel class."""
+    out = (ctypes.c_double * 4)()
+    _check(_lib.lmvd_profile_read(h, int(cls), out), "lmvd_profile_read")
+    return tuple(out)
+
+
+def lmvd_kernel_class_name(cls):
+    return _lib.lmvd_kernel_class_name(int(cls)).decode()
+
+
+def lmvd_kernel_launches(h):
+    return int(_lib.lmvd_kernel_launches(h))
 
 
 # ---------------------------------------------------------------- convenience (still marshalling only)

@@ -30,6 +30,8 @@ import numpy as np
 WORKLOADS = {
     "rt32": dict(nx=32, ny=33, nz=32, ratio=3.0, width=0.05, kmax=4, eta_rms=1e-2, u_rms=1e-4,
                  re=1000.0, dt=1e-3, steps=5, seed=1001),
+    "rt128": dict(nx=128, ny=129, nz=128, ratio=3.0, width=0.05, kmax=8, eta_rms=1e-2, u_rms=1e-4,
+                  re=1000.0, dt=5e-4, steps=20, seed=1004),
     "rt256": dict(nx=256, ny=257, nz=256, ratio=25.7, width=0.02, kmax=16, eta_rms=5e-3, u_rms=1e-4,
                   re=3000.0, dt=2e-4, steps=20, seed=1002),
     "rt512": dict(nx=512, ny=513, nz=512, ratio=10.0, width=0.05, kmax=32, eta_rms=2e-3, u_rms=1e-4,
