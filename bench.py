@@ -181,6 +181,18 @@ def gpu_index(local):
     return str(local)
 
 
+# ------------------------------------------------------------------ multi-rank aggregation
+def aggregate(ms_local, units_per_rank, world, device=None):
+    """Slowest rank's time and the whole-job rate: value = units of all ranks / max time."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms_local)], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    return ms_max, units_per_rank * world / (ms_max / 1e3) / 1e6
+
+
 # ------------------------------------------------------------------ CUDA arm
 def run_cuda(args):
     import numpy as np
@@ -230,11 +242,7 @@ def run_cuda(args):
     launches = L.lmvd_kernel_launches(ctx.h) - launches0
     prof = {L.lmvd_kernel_class_name(c): L.lmvd_profile_read(ctx.h, c) for c in range(L.LMVD_KERNEL_CLASSES)}
     L.lmvd_profile_enable(ctx.h, False)
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = npts * args.steps * ws / (ms_max / 1e3) / 1e6
+    ms_max, value = aggregate(ms, npts * args.steps, ws, device="cuda")
 
     # dominant kernel class: roofline (FFT passes are FP64-ALU bound on GB300)
     top = max(prof, key=lambda k: prof[k][0])
@@ -272,10 +280,7 @@ def run_cuda(args):
         ctx.get_state(host_out, history=hist_out)
         ctx.synchronize()
     e2e_s = time.perf_counter() - t0
-    te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = npts * args.e2e_steps * ws / float(te.item()) / 1e6 if args.e2e_steps > 0 else None
+    e2e_value = aggregate(1e3 * e2e_s, npts * args.e2e_steps, ws, device="cuda")[1] if args.e2e_steps > 0 else None
     ctx.close()
 
     out = {
