@@ -33,8 +33,14 @@ UNIT = "Mpoints*substages/s"
 # FP64 peak of GB300 from this pool's measurement: 0.596e12 DFMA/s at 1.99 GHz across 152 SMs is
 # 2 DFMA/clk/SM; at the 2070 MHz maximum SM clock: 152 * 2 * 2 flop * 2.07e9 = 1.259 TFLOP/s.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
-# DRAM bytes per launch of the dominant kernel from one ncu capture (None until captured for this code)
-NCU_TRAFFIC_PER_LAUNCH = None
+# FP64-equivalent peak of double-float arithmetic on the FP32 pipe: a radix-2 butterfly (10 classic
+# flops: one complex multiply, two complex adds) costs 2 x 22 + 4 x 14 = 100 FP32 instructions in
+# df64.h (TwoSum-renormalised adds, FMA TwoProd products), i.e. 10 instructions per classic flop;
+# the FP32 pipe issues 152 SMs x 128 lanes x 2.07 GHz instructions per second.
+DF64_EQ_PEAK_TFLOPS = 152 * 128 * 2.07e9 / 10 / 1e12
+# DRAM bytes per launch of the dominant kernel from one ncu capture, by precision (None until captured
+# for the current code of that kernel)
+NCU_TRAFFIC_PER_LAUNCH = {0: None, 1: None}
 CPU_SAMPLE_N = 128
 
 
@@ -47,6 +53,8 @@ def parse():
     ap.add_argument("--workload", default="rt512")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", type=int, default=0, help="0: FP64; 1: double-float transforms/products")
+    ap.add_argument("--no-variant", action="store_true", help="skip timing the other precision")
     return ap.parse_args()
 
 
@@ -194,33 +202,19 @@ def aggregate(ms_local, units_per_rank, world, device=None):
 
 
 # ------------------------------------------------------------------ CUDA arm
-def run_cuda(args):
-    import numpy as np
+def time_variant(L, w, precision, args, stream, st_host, local, ws, e2e_steps=0):
+    """Create a context, run warm-up + K timed substages (CUDA events on the library stream), read the
+    per-class profile, optionally the end-to-end loop; return (result dict, final state on the host)."""
     import torch
     import torch.distributed as dist
 
-    from paper_2206_09878_gb300 import lmvd as L
-    from paper_2206_09878_gb300.rt_inputs import rt_state
-
-    ws, rank, local = dist_env()
-    torch.cuda.set_device(local)
-    if ws > 1:
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    w, config = workload_config(args.workload)
-    config["parallelism"] = "replicas%d" % ws if ws > 1 else "single"
-    npts = w["nx"] * w["ny"] * w["nz"]
     cfg = L.lmvd_default_config(w["nx"], w["ny"], w["nz"], re=w["re"], rho_light=1.0 / w["ratio"], dt=w["dt"],
-                                n_startup=4)
-    stream = torch.cuda.Stream()
+                                n_startup=4, precision=precision)
     ctx = L.Context(cfg, stream=stream)
-    st = {k: torch.from_numpy(np.ascontiguousarray(v)) for k, v in rt_state(**w).items()}
-    dev = {k: v.cuda() for k, v in st.items()}
-    ctx.set_state(dev)
+    ctx.set_state({k: v.cuda() for k, v in st_host.items()})
     for _ in range(args.warmup):
         ctx.advance_substage()
     ctx.synchronize()
-
-    # ---- timed region: K substages, state resident in HBM
     L.lmvd_profile_enable(ctx.h, True)
     launches0 = L.lmvd_kernel_launches(ctx.h)
     clocks = ClockSampler(gpu_index(local))
@@ -242,56 +236,106 @@ def run_cuda(args):
     launches = L.lmvd_kernel_launches(ctx.h) - launches0
     prof = {L.lmvd_kernel_class_name(c): L.lmvd_profile_read(ctx.h, c) for c in range(L.LMVD_KERNEL_CLASSES)}
     L.lmvd_profile_enable(ctx.h, False)
-    ms_max, value = aggregate(ms, npts * args.steps, ws, device="cuda")
+    final = {k: v.cpu() for k, v in ctx.get_state().items()}
+    ctx.synchronize()
+    res = dict(ms=ms, clocks=ck, launches=launches, prof=prof)
+    if e2e_steps > 0:
+        host_in = {k: v.pin_memory() for k, v in st_host.items()}
+        hist_dev = ctx.history_buffer()
+        ctx.get_state(history=hist_dev)
+        hist_in = hist_dev.cpu().pin_memory()
+        host_out = ctx.empty_state("cpu", pin=True)
+        hist_out = torch.empty_like(hist_in).pin_memory()
+        ctx.synchronize()
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            ctx.set_state(host_in, history=hist_in)
+            ctx.advance_substage()
+            ctx.get_state(host_out, history=hist_out)
+            ctx.synchronize()
+        res["e2e_s"] = time.perf_counter() - t0
+        res["e2e_bytes"] = sum(v.numel() * v.element_size() for v in host_in.values()) + hist_in.numel()
+    ctx.close()
+    return res, final
 
-    # dominant kernel class: roofline (FFT passes are FP64-ALU bound on GB300)
+
+def roofline_of(prof, ms_step_total, fp):
+    """Dominant kernel class and its achieved algorithmic rate against the ALU peak of its arithmetic."""
     top = max(prof, key=lambda k: prof[k][0])
     tms, tn, tfl, tby = prof[top]
     achieved = tfl / (tms / 1e3) / 1e12 if tms > 0 else None
-    roofline = {"kernel": top, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS if achieved else None,
-                "traffic": NCU_TRAFFIC_PER_LAUNCH, "launches": int(tn),
-                "algorithmic_bytes_per_launch": tby / tn if tn else None,
-                "achieved_hbm_gbs": tby / (tms / 1e3) / 1e9 if tms > 0 else None,
-                "peak_note": "FP64 peak derived: 152 SMs x 2 DFMA/clk/SM (measured) x 2 flop x 2.07 GHz",
-                "share_of_step": tms / ms if ms > 0 else None}
+    if fp == 0:
+        peak, note = FP64_PEAK_TFLOPS, "FP64 peak derived: 152 SMs x 2 DFMA/clk/SM (measured) x 2 flop x 2.07 GHz"
+    else:
+        peak, note = DF64_EQ_PEAK_TFLOPS, ("FP64-equivalent peak of double-float on the FP32 pipe: 152 SMs x 128 "
+                                            "lanes x 2.07 GHz / 10 FP32 instructions per classic flop")
+    return {"kernel": top, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak if achieved else None, "traffic": NCU_TRAFFIC_PER_LAUNCH.get(fp),
+            "launches": int(tn), "algorithmic_bytes_per_launch": tby / tn if tn else None,
+            "achieved_hbm_gbs": tby / (tms / 1e3) / 1e9 if tms > 0 else None, "peak_note": note,
+            "share_of_step": tms / ms_step_total if ms_step_total > 0 else None}
+
+
+def rel_err(a, b):
+    import torch
+    return float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
+
+
+def run_cuda(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2206_09878_gb300 import lmvd as L
+    from paper_2206_09878_gb300.rt_inputs import rt_state
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    w, config = workload_config(args.workload)
+    config["parallelism"] = "replicas%d" % ws if ws > 1 else "single"
+    config["precision"] = ("FP64 throughout" if args.precision == 0 else
+                           "double-float transforms and products, FP64 spectral steps")
+    npts = w["nx"] * w["ny"] * w["nz"]
+    stream = torch.cuda.Stream()
+    st = {k: torch.from_numpy(np.ascontiguousarray(v)) for k, v in rt_state(**w).items()}
+
+    res, final = time_variant(L, w, args.precision, args, stream, st, local, ws, e2e_steps=args.e2e_steps)
+    ms_max, value = aggregate(res["ms"], npts * args.steps, ws, device="cuda")
+    prof = res["prof"]
     breakdown = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps,
                      "tflops": (v[2] / (v[0] / 1e3) / 1e12) if v[0] > 0 else None,
                      "hbm_gbs": (v[3] / (v[0] / 1e3) / 1e9) if v[0] > 0 else None}
                  for k, v in prof.items() if v[1] > 0}
-
-    # ---- end to end through the public API with pinned host buffers
-    host_in = {k: v.pin_memory() for k, v in st.items()}
-    hist_dev = ctx.history_buffer()
-    ctx.get_state(history=hist_dev)
-    hist_in = hist_dev.cpu().pin_memory()
-    host_out = ctx.empty_state("cpu", pin=True)
-    hist_out = torch.empty_like(hist_in).pin_memory()
-    ctx.synchronize()
-    state_bytes = sum(v.numel() * v.element_size() for v in host_in.values())
-    hbytes = hist_in.numel()
-    if ws > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(args.e2e_steps):
-        ctx.set_state(host_in, history=hist_in)
-        ctx.advance_substage()
-        ctx.get_state(host_out, history=hist_out)
-        ctx.synchronize()
-    e2e_s = time.perf_counter() - t0
-    e2e_value = aggregate(1e3 * e2e_s, npts * args.e2e_steps, ws, device="cuda")[1] if args.e2e_steps > 0 else None
-    ctx.close()
-
+    e2e = None
+    if args.e2e_steps > 0:
+        e2e_value = aggregate(1e3 * res["e2e_s"], npts * args.e2e_steps, ws, device="cuda")[1]
+        e2e = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": res["e2e_bytes"],
+               "d2h_bytes_per_step": res["e2e_bytes"], "steps": args.e2e_steps}
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic (seeded Rayleigh-Taylor-shaped state)", "config": config,
-        "clocks": ck, "gpu_launches": int(launches), "roofline": roofline,
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": state_bytes + hbytes,
-                "d2h_bytes_per_step": state_bytes + hbytes, "steps": args.e2e_steps},
-        "kernels": breakdown,
+        "clocks": res["clocks"], "gpu_launches": int(res["launches"]),
+        "roofline": roofline_of(prof, res["ms"], args.precision), "e2e": e2e, "kernels": breakdown,
     }
+    if not args.no_variant:
+        other = 1 - args.precision
+        r2, f2 = time_variant(L, w, other, args, stream, st, local, ws)
+        _, v2 = aggregate(r2["ms"], npts * args.steps, ws, device="cuda")
+        errs = {k: rel_err(f2[k], final[k]) for k in ("z", "om", "m2")}
+        out["variant"] = {
+            "precision": ("FP64 throughout" if other == 0 else
+                          "FP32-FFT: double-float (2 x FP32, error-free transformations) transforms and products, "
+                          "FP64 solves / RHS / update"),
+            "value": v2, "unit": UNIT, "ms_per_step": r2["ms"] / args.steps, "clocks": r2["clocks"],
+            "roofline": roofline_of(r2["prof"], r2["ms"], other),
+            "state_rel_l2_vs_headline_after_%d_substages" % (args.warmup + args.steps): errs,
+        }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         rate, cores, desc = oracle_rate(w, 2)
         out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}

@@ -56,6 +56,10 @@ extern "C" {
  * kf          : fixed-point applications of L per substage (Sec. 3.2).
  * beta_n, beta_p: free parameters of the guesses of Eq. dzdt_guesses (paper: 0 and -4).
  * n_startup   : fixed-point iterations from dz/dt = 0 used by lmvd_set_state without history.
+ * precision   : 0 = FP64 throughout; 1 = transforms and physical-space products in double-float
+ *               arithmetic on the FP32 units (pairs of floats, 48-bit significand, error-free
+ *               TwoSum/TwoProd compensation), while every spectral step (collocation, m^c and m2^d
+ *               solves, RHS assembly, the RK update and the state) stays FP64.
  */
 typedef struct {
   int nx, ny, nz, spline_order;
@@ -65,12 +69,14 @@ typedef struct {
   int kf;
   double beta_n, beta_p;
   int n_startup;
+  int precision;
 } lmvd_config;
 
 typedef struct lmvd_ctx lmvd_ctx;
 
 /* Fill *cfg with the defaults (p = 6, 2 pi periods, walls at -1 and +1, Re = 1000, Sc = Fr = 1,
- * density ratio 3, dt = 1e-3, kf = 4, beta_n = 0, beta_p = -4, n_startup = 20) for the given grid.
+ * density ratio 3, dt = 1e-3, kf = 4, beta_n = 0, beta_p = -4, n_startup = 20, precision = 0) for
+ * the given grid.
  * Returns LMVD_ERR_INVALID_ARG if cfg is NULL. */
 int lmvd_default_config(lmvd_config* cfg, int nx, int ny, int nz);
 

@@ -292,9 +292,14 @@ void physical_pass_1(Ctx& c) {
   fft_inverse(c, in, out, 8);
   const size_t n = (size_t)c.g.ny * c.g.P;
   EosArgs e{c.cfg.rho_heavy, c.cfg.rho_light, 1.0 / (c.cfg.re * c.cfg.sc)};
-  LMVD_LAUNCH(c, KC_PRODUCTS, 25.0 * n, 8.0 * 15 * n, k_products_p1, elem_blocks(n), 256, 0, n, e, c.pw[0], c.pw[1],
-              c.pw[2], c.pw[3], c.pw[4], c.md[0], c.md[1], c.md[2], c.rho, c.invrho, c.fprime, c.w[0], c.w[1],
-              c.w[2], c.pw[5]);
+  if (c.cfg.precision == 1)
+    LMVD_LAUNCH(c, KC_PRODUCTS, 25.0 * n, 8.0 * 15 * n, k_products_p1_df, elem_blocks(n), 256, 0, n, e, c.pw[0],
+                c.pw[1], c.pw[2], c.pw[3], c.pw[4], c.md[0], c.md[1], c.md[2], c.rho, c.invrho, c.fprime, c.w[0],
+                c.w[1], c.w[2], c.pw[5]);
+  else
+    LMVD_LAUNCH(c, KC_PRODUCTS, 25.0 * n, 8.0 * 15 * n, k_products_p1, elem_blocks(n), 256, 0, n, e, c.pw[0],
+                c.pw[1], c.pw[2], c.pw[3], c.pw[4], c.md[0], c.md[1], c.md[2], c.rho, c.invrho, c.fprime, c.w[0],
+                c.w[1], c.w[2], c.pw[5]);
   double* fin[1] = {c.pw[5]};
   cd* fout[1] = {c.sv[0]};
   fft_forward(c, fin, fout, 1);
@@ -310,7 +315,11 @@ void mc_from_zdot(Ctx& c) {
     double* out[1] = {c.pw[0]};
     fft_inverse(c, in, out, 1);
   }
-  LMVD_LAUNCH(c, KC_PRODUCTS, 1.0 * n, 24.0 * n, k_product_rt, elem_blocks(n), 256, 0, n, c.fprime, c.pw[0], c.pw[1]);
+  if (c.cfg.precision == 1)
+    LMVD_LAUNCH(c, KC_PRODUCTS, 1.0 * n, 24.0 * n, k_product_rt_df, elem_blocks(n), 256, 0, n, c.fprime, c.pw[0],
+                c.pw[1]);
+  else
+    LMVD_LAUNCH(c, KC_PRODUCTS, 1.0 * n, 24.0 * n, k_product_rt, elem_blocks(n), 256, 0, n, c.fprime, c.pw[0], c.pw[1]);
   {
     double* in[1] = {c.pw[1]};
     cd* out[1] = {c.sv[1]};
@@ -333,8 +342,12 @@ void mc_from_zdot(Ctx& c) {
 void fp_apply(Ctx& c) {
   mc_from_zdot(c);
   const size_t n = (size_t)c.g.ny * c.g.P;
-  LMVD_LAUNCH(c, KC_PRODUCTS, 6.0 * n, 56.0 * n, k_product_L, elem_blocks(n), 256, 0, n, c.w[0], c.w[1], c.w[2],
-              c.pw[0], c.pw[1], c.pw[2], c.pw[3]);
+  if (c.cfg.precision == 1)
+    LMVD_LAUNCH(c, KC_PRODUCTS, 6.0 * n, 56.0 * n, k_product_L_df, elem_blocks(n), 256, 0, n, c.w[0], c.w[1], c.w[2],
+                c.pw[0], c.pw[1], c.pw[2], c.pw[3]);
+  else
+    LMVD_LAUNCH(c, KC_PRODUCTS, 6.0 * n, 56.0 * n, k_product_L, elem_blocks(n), 256, 0, n, c.w[0], c.w[1], c.w[2],
+                c.pw[0], c.pw[1], c.pw[2], c.pw[3]);
   double* in[1] = {c.pw[3]};
   cd* out[1] = {c.sv[3]};
   fft_forward(c, in, out, 1);
@@ -380,8 +393,12 @@ int advance(Ctx& c) {
   // steps 4-5: products with m = m^d + m^c, forward transforms, RHS streams, collocation solves, RHS
   P2Out q{};
   for (int f = 0; f < 10; ++f) q.p[f] = c.pw[f];
-  LMVD_LAUNCH(c, KC_PRODUCTS, 18.0 * n, 8.0 * 18 * n, k_products_p2, elem_blocks(n), 256, 0, n, c.md[0], c.md[1],
-              c.md[2], c.pw[0], c.pw[1], c.pw[2], c.rho, c.invrho, q);
+  if (cf.precision == 1)
+    LMVD_LAUNCH(c, KC_PRODUCTS, 18.0 * n, 8.0 * 18 * n, k_products_p2_df, elem_blocks(n), 256, 0, n, c.md[0],
+                c.md[1], c.md[2], c.pw[0], c.pw[1], c.pw[2], c.rho, c.invrho, q);
+  else
+    LMVD_LAUNCH(c, KC_PRODUCTS, 18.0 * n, 8.0 * 18 * n, k_products_p2, elem_blocks(n), 256, 0, n, c.md[0], c.md[1],
+                c.md[2], c.pw[0], c.pw[1], c.pw[2], c.rho, c.invrho, q);
   fft_forward(c, c.pw, c.sv, 10);
   Fields10C svc{};
   for (int f = 0; f < 10; ++f) svc.p[f] = c.sv[f];
@@ -443,6 +460,7 @@ bool valid_cfg(const lmvd_config& f) {
   if (!(f.lx > 0) || !(f.lz > 0) || !(f.y1 > f.y0)) return false;
   if (!(f.re > 0) || !(f.sc > 0) || !(f.fr > 0) || !(f.rho_heavy > 0) || !(f.rho_light > 0)) return false;
   if (!(f.dt > 0) || f.kf < 0 || f.n_startup < 0) return false;
+  if (f.precision != 0 && f.precision != 1) return false;
   return true;
 }
 

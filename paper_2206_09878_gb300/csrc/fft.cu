@@ -11,11 +11,16 @@
 //            then z-pass (complex, truncated, scaled by 1/(px pz)).
 // Synthesis is unnormalised: f(x, z) = sum_k fhat_k exp(i (k1 x + k3 z)).
 // A pass is one CTA per (plane, field, batch of columns / row pairs); every 1D transform is a
-// Stockham autosort FFT in shared memory with radix-4/3/2 stages and a double-precision twiddle
-// table.
+// Stockham autosort FFT in shared memory with radix-4/3/2 stages and a precomputed twiddle table.
+//
+// Arithmetic: complex double (precision 0) or complex double-float (precision 1, df64.h) selected
+// by the complex type C. Spectral inputs and outputs are always complex double; the intermediate
+// T and the physical fields are stored in the arithmetic's own type (double, or hi/lo float pairs
+// of the same size), so the double-float path converts only at the spectral ends.
 #include <cmath>
 #include <cstring>
 
+#include "df64.h"
 #include "lmvd_internal.h"
 
 namespace lmvd {
@@ -27,19 +32,83 @@ struct FieldsW {
   cd* p[10];
 };
 struct FieldsRC {
-  const double* p[10];
+  const void* p[10];
 };
 struct FieldsRW {
-  double* p[10];
+  void* p[10];
+};
+
+// ------------------------------------------------------------------ arithmetic traits
+template <class C>
+struct FT;
+
+template <>
+struct FT<cd> {
+  using R = double;
+  __device__ static cd zero() { return mk(0, 0); }
+  __device__ static cd add(cd a, cd b) { return a + b; }
+  __device__ static cd sub(cd a, cd b) { return a - b; }
+  __device__ static cd ti(cd a) { return times_i(a); }
+  __device__ static cd neg(cd a) { return cd{-a.re, -a.im}; }
+  __device__ static cd cj(cd a) { return conj(a); }
+  __device__ static cd half(cd a) { return 0.5 * a; }
+  template <int SIGN>
+  __device__ static cd mulw(cd v, const FFTPlan& p, int idx) {
+    const double2 w = p.tw[idx];
+    return cmul(v, cd{w.x, SIGN * w.y});
+  }
+  template <int SIGN>
+  __device__ static cd mul_s3(cd v, const FFTPlan&) {  // SIGN sin(2 pi / 3) v
+    return (SIGN * 0.86602540378443864676372317075294) * v;
+  }
+  __device__ static cd from_spec(cd x) { return x; }
+  __device__ static cd to_spec(cd x, const FFTPlan& p) { return p.scale_d * x; }
+  __device__ static cd make(R a, R b) { return cd{a, b}; }
+  __device__ static R re(cd a) { return a.re; }
+  __device__ static R im(cd a) { return a.im; }
+  __device__ static R rzero() { return 0.0; }
+};
+
+template <>
+struct FT<cdf> {
+  using R = df;
+  __device__ static cdf zero() { return cdf{df{0.f, 0.f}, df{0.f, 0.f}}; }
+  __device__ static cdf add(cdf a, cdf b) { return cadd(a, b); }
+  __device__ static cdf sub(cdf a, cdf b) { return csub(a, b); }
+  __device__ static cdf ti(cdf a) { return ctimes_i(a); }
+  __device__ static cdf neg(cdf a) { return cdf{dneg(a.re), dneg(a.im)}; }
+  __device__ static cdf cj(cdf a) { return cconj(a); }
+  __device__ static cdf half(cdf a) { return cdf{dscale2(a.re, 0.5f), dscale2(a.im, 0.5f)}; }
+  template <int SIGN>
+  __device__ static cdf mulw(cdf v, const FFTPlan& p, int idx) {
+    const float4 w = p.twf[idx];
+    const df wr{w.x, w.y};
+    const df wi = SIGN > 0 ? df{w.z, w.w} : df{-w.z, -w.w};
+    return cmulw(v, wr, wi);
+  }
+  template <int SIGN>
+  __device__ static cdf mul_s3(cdf v, const FFTPlan& p) {
+    const df s = SIGN > 0 ? p.s3f : dneg(p.s3f);
+    return cdf{dmul(v.re, s), dmul(v.im, s)};
+  }
+  __device__ static cdf from_spec(cd x) { return cdf{df_from_double(x.re), df_from_double(x.im)}; }
+  __device__ static cd to_spec(cdf x, const FFTPlan& p) {
+    return cd{df_to_double(dmul(x.re, p.scale_f)), df_to_double(dmul(x.im, p.scale_f))};
+  }
+  __device__ static cdf make(R a, R b) { return cdf{a, b}; }
+  __device__ static R re(cdf a) { return a.re; }
+  __device__ static R im(cdf a) { return a.im; }
+  __device__ static R rzero() { return df{0.f, 0.f}; }
 };
 
 // One Stockham stage set on a batch of transforms of length n stored with leading dimension ld.
-// sign = +1: synthesis (exp(+i)), -1: analysis. Returns the buffer holding the result.
-template <int SIGN>
-__device__ cd* fft_batch(cd* a, cd* b, const FFTPlan& pl, int batch, int ld) {
+// SIGN = +1: synthesis (exp(+i)), -1: analysis. Returns the buffer holding the result.
+template <class C, int SIGN>
+__device__ C* fft_batch(C* a, C* b, const FFTPlan& pl, int batch, int ld) {
+  using F = FT<C>;
   const int n = pl.n;
-  cd* in = a;
-  cd* out = b;
+  C* in = a;
+  C* out = b;
   int L = 1;
   for (int s = 0; s < pl.nst; ++s) {
     const int r = pl.radix[s];
@@ -50,42 +119,44 @@ __device__ cd* fft_batch(cd* a, cd* b, const FFTPlan& pl, int batch, int ld) {
       const int bt = t / nb;
       const int i = t - bt * nb;
       const int k = i % L;
-      const cd* src = in + bt * ld;
-      cd* dst = out + bt * ld;
-      cd v[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q)
-        if (q < r) v[q] = src[i + q * nb];
-#pragma unroll
-      for (int q = 1; q < 4; ++q)
-        if (q < r) {
-          const double2 w = pl.tw[q * k * tws];
-          v[q] = cmul(v[q], cd{w.x, SIGN * w.y});
-        }
+      const C* src = in + bt * ld;
+      C* dst = out + bt * ld;
       const int base = (i - k) * r + k;
       if (r == 4) {
-        const cd t0 = v[0] + v[2], t1 = v[0] - v[2], t2 = v[1] + v[3];
-        const cd d3 = times_i(v[1] - v[3]);
-        const cd t3 = SIGN > 0 ? d3 : cd{-d3.re, -d3.im};  // (SIGN i) (v1 - v3)
-        dst[base] = t0 + t2;
-        dst[base + L] = t1 + t3;
-        dst[base + 2 * L] = t0 - t2;
-        dst[base + 3 * L] = t1 - t3;
+        C v0 = src[i], v1 = src[i + nb], v2 = src[i + 2 * nb], v3 = src[i + 3 * nb];
+        if (k) {
+          v1 = F::template mulw<SIGN>(v1, pl, k * tws);
+          v2 = F::template mulw<SIGN>(v2, pl, 2 * k * tws);
+          v3 = F::template mulw<SIGN>(v3, pl, 3 * k * tws);
+        }
+        const C t0 = F::add(v0, v2), t1 = F::sub(v0, v2), t2 = F::add(v1, v3);
+        const C d3 = F::ti(F::sub(v1, v3));
+        const C t3 = SIGN > 0 ? d3 : F::neg(d3);  // (SIGN i) (v1 - v3)
+        dst[base] = F::add(t0, t2);
+        dst[base + L] = F::add(t1, t3);
+        dst[base + 2 * L] = F::sub(t0, t2);
+        dst[base + 3 * L] = F::sub(t1, t3);
       } else if (r == 3) {
-        const double sn = SIGN * 0.86602540378443864676372317075294;  // sin(2 pi / 3)
-        const cd t1 = v[1] + v[2], t2 = v[1] - v[2];
-        const cd m = v[0] - 0.5 * t1;
-        const cd u = sn * times_i(t2);
-        dst[base] = v[0] + t1;
-        dst[base + L] = m + u;
-        dst[base + 2 * L] = m - u;
+        C v0 = src[i], v1 = src[i + nb], v2 = src[i + 2 * nb];
+        if (k) {
+          v1 = F::template mulw<SIGN>(v1, pl, k * tws);
+          v2 = F::template mulw<SIGN>(v2, pl, 2 * k * tws);
+        }
+        const C t1 = F::add(v1, v2);
+        const C m = F::sub(v0, F::half(t1));
+        const C u = F::ti(F::template mul_s3<SIGN>(F::sub(v1, v2), pl));
+        dst[base] = F::add(v0, t1);
+        dst[base + L] = F::add(m, u);
+        dst[base + 2 * L] = F::sub(m, u);
       } else {
-        dst[base] = v[0] + v[1];
-        dst[base + L] = v[0] - v[1];
+        C v0 = src[i], v1 = src[i + nb];
+        if (k) v1 = F::template mulw<SIGN>(v1, pl, k * tws);
+        dst[base] = F::add(v0, v1);
+        dst[base + L] = F::sub(v0, v1);
       }
     }
     __syncthreads();
-    cd* tmp = in;
+    C* tmp = in;
     in = out;
     out = tmp;
     L = Ls;
@@ -94,26 +165,29 @@ __device__ cd* fft_batch(cd* a, cd* b, const FFTPlan& pl, int batch, int ld) {
 }
 
 // ---------------------------------------------------------------- inverse z-pass
-// in: spectral value fields [ny][nz][nxh]; T: [f][ny][pz][nx/2]
-__global__ void k_fft_z_inv(FFTPlan pl, Grid g, FieldsC in, cd* T, size_t tstride) {
-  extern __shared__ cd sm[];
+// in: spectral value fields [ny][nz][nxh] (complex double); T: [f][ny][pz][nx/2] of C
+template <class C>
+__global__ void k_fft_z_inv(FFTPlan pl, Grid g, FieldsC in, C* T, size_t tstride) {
+  using F = FT<C>;
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  C* sm = reinterpret_cast<C*>(sm_raw);
   const int batch = pl.batch, ld = pl.n + 1, pz = g.pz, nz = g.nz, h = g.nx / 2;
   const int kx0 = blockIdx.x * batch, j = blockIdx.y, f = blockIdx.z;
-  cd* a = sm;
-  cd* b = sm + batch * ld;
-  for (int idx = threadIdx.x; idx < batch * ld; idx += blockDim.x) a[idx] = mk(0, 0);
+  C* a = sm;
+  C* b = sm + batch * ld;
+  for (int idx = threadIdx.x; idx < batch * ld; idx += blockDim.x) a[idx] = F::zero();
   __syncthreads();
   const cd* src = in.p[f] + (size_t)j * g.M;
   for (int idx = threadIdx.x; idx < nz * batch; idx += blockDim.x) {
     const int jz = idx / batch, bb = idx - jz * batch, kx = kx0 + bb;
     if (kx < h && jz != nz / 2) {
       const int pos = jz < nz / 2 ? jz : pz - nz + jz;
-      a[bb * ld + pos] = src[(size_t)jz * g.nxh + kx];
+      a[bb * ld + pos] = F::from_spec(src[(size_t)jz * g.nxh + kx]);
     }
   }
   __syncthreads();
-  const cd* res = fft_batch<1>(a, b, pl, batch, ld);
-  cd* dst = T + f * tstride + (size_t)j * pz * h;
+  const C* res = fft_batch<C, 1>(a, b, pl, batch, ld);
+  C* dst = T + f * tstride + (size_t)j * pz * h;
   for (int idx = threadIdx.x; idx < pz * batch; idx += blockDim.x) {
     const int zz = idx / batch, bb = idx - zz * batch, kx = kx0 + bb;
     if (kx < h) dst[(size_t)zz * h + kx] = res[bb * ld + zz];
@@ -121,96 +195,105 @@ __global__ void k_fft_z_inv(FFTPlan pl, Grid g, FieldsC in, cd* T, size_t tstrid
 }
 
 // ---------------------------------------------------------------- inverse x-pass (c2r, 2 rows per transform)
-__global__ void k_fft_x_inv(FFTPlan pl, Grid g, const cd* T, size_t tstride, FieldsRW out) {
-  extern __shared__ cd sm[];
+template <class C>
+__global__ void k_fft_x_inv(FFTPlan pl, Grid g, const C* T, size_t tstride, FieldsRW out) {
+  using F = FT<C>;
+  using R = typename F::R;
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  C* sm = reinterpret_cast<C*>(sm_raw);
   const int batch = pl.batch, ld = pl.n + 1, px = g.px, pz = g.pz, h = g.nx / 2;
   const int pr0 = blockIdx.x * batch, j = blockIdx.y, f = blockIdx.z;
-  cd* a = sm;
-  cd* b = sm + batch * ld;
-  for (int idx = threadIdx.x; idx < batch * ld; idx += blockDim.x) a[idx] = mk(0, 0);
+  C* a = sm;
+  C* b = sm + batch * ld;
+  for (int idx = threadIdx.x; idx < batch * ld; idx += blockDim.x) a[idx] = F::zero();
   __syncthreads();
-  const cd* src = T + f * tstride + (size_t)j * pz * h;
+  const C* src = T + f * tstride + (size_t)j * pz * h;
   for (int idx = threadIdx.x; idx < batch * h; idx += blockDim.x) {
     const int bb = idx / h, k = idx - bb * h;
     const int za = 2 * (pr0 + bb), zb = za + 1;
     if (za >= pz) continue;
-    const cd ta = src[(size_t)za * h + k];
-    const cd tb = zb < pz ? src[(size_t)zb * h + k] : mk(0, 0);
-    cd* y = a + bb * ld;
+    const C ta = src[(size_t)za * h + k];
+    const C tb = zb < pz ? src[(size_t)zb * h + k] : F::zero();
+    C* y = a + bb * ld;
     if (k == 0) {
-      y[0] = mk(ta.re, tb.re);  // the kx = 0 coefficient of a real row is real
+      y[0] = F::make(F::re(ta), F::re(tb));  // the kx = 0 coefficient of a real row is real
     } else {
-      y[k] = mk(ta.re - tb.im, ta.im + tb.re);       // Xa[k] + i Xb[k]
-      y[px - k] = mk(ta.re + tb.im, tb.re - ta.im);  // conj(Xa[k]) + i conj(Xb[k])
+      y[k] = F::add(ta, F::ti(tb));                     // Xa[k] + i Xb[k]
+      y[px - k] = F::add(F::cj(ta), F::ti(F::cj(tb)));  // conj(Xa[k]) + i conj(Xb[k])
     }
   }
   __syncthreads();
-  const cd* res = fft_batch<1>(a, b, pl, batch, ld);
-  double* dst = out.p[f] + (size_t)j * g.P;
+  const C* res = fft_batch<C, 1>(a, b, pl, batch, ld);
+  R* dst = reinterpret_cast<R*>(out.p[f]) + (size_t)j * g.P;
   for (int idx = threadIdx.x; idx < batch * px; idx += blockDim.x) {
     const int bb = idx / px, x = idx - bb * px;
     const int za = 2 * (pr0 + bb), zb = za + 1;
     if (za >= pz) continue;
-    const cd v = res[bb * ld + x];
-    dst[(size_t)za * px + x] = v.re;
-    if (zb < pz) dst[(size_t)zb * px + x] = v.im;
+    const C v = res[bb * ld + x];
+    dst[(size_t)za * px + x] = F::re(v);
+    if (zb < pz) dst[(size_t)zb * px + x] = F::im(v);
   }
 }
 
 // ---------------------------------------------------------------- forward x-pass (r2c, 2 rows per transform)
-__global__ void k_fft_x_fwd(FFTPlan pl, Grid g, FieldsRC in, cd* T, size_t tstride) {
-  extern __shared__ cd sm[];
+template <class C>
+__global__ void k_fft_x_fwd(FFTPlan pl, Grid g, FieldsRC in, C* T, size_t tstride) {
+  using F = FT<C>;
+  using R = typename F::R;
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  C* sm = reinterpret_cast<C*>(sm_raw);
   const int batch = pl.batch, ld = pl.n + 1, px = g.px, pz = g.pz, h = g.nx / 2;
   const int pr0 = blockIdx.x * batch, j = blockIdx.y, f = blockIdx.z;
-  cd* a = sm;
-  cd* b = sm + batch * ld;
-  const double* src = in.p[f] + (size_t)j * g.P;
+  C* a = sm;
+  C* b = sm + batch * ld;
+  const R* src = reinterpret_cast<const R*>(in.p[f]) + (size_t)j * g.P;
   for (int idx = threadIdx.x; idx < batch * px; idx += blockDim.x) {
     const int bb = idx / px, x = idx - bb * px;
     const int za = 2 * (pr0 + bb), zb = za + 1;
-    double va = 0.0, vb = 0.0;
+    R va = F::rzero(), vb = F::rzero();
     if (za < pz) {
       va = src[(size_t)za * px + x];
       if (zb < pz) vb = src[(size_t)zb * px + x];
     }
-    a[bb * ld + x] = mk(va, vb);
+    a[bb * ld + x] = F::make(va, vb);
   }
   __syncthreads();
-  const cd* res = fft_batch<-1>(a, b, pl, batch, ld);
-  cd* dst = T + f * tstride + (size_t)j * pz * h;
+  const C* res = fft_batch<C, -1>(a, b, pl, batch, ld);
+  C* dst = T + f * tstride + (size_t)j * pz * h;
   for (int idx = threadIdx.x; idx < batch * h; idx += blockDim.x) {
     const int bb = idx / h, k = idx - bb * h;
     const int za = 2 * (pr0 + bb), zb = za + 1;
     if (za >= pz) continue;
-    const cd yk = res[bb * ld + k];
-    const cd ym = conj(res[bb * ld + (k == 0 ? 0 : px - k)]);
-    const cd fa = 0.5 * (yk + ym);
-    const cd d = yk - ym;
-    dst[(size_t)za * h + k] = fa;
-    if (zb < pz) dst[(size_t)zb * h + k] = mk(0.5 * d.im, -0.5 * d.re);  // (yk - ym) / (2 i)
+    const C yk = res[bb * ld + k];
+    const C ym = F::cj(res[bb * ld + (k == 0 ? 0 : px - k)]);
+    dst[(size_t)za * h + k] = F::half(F::add(yk, ym));
+    if (zb < pz) dst[(size_t)zb * h + k] = F::neg(F::ti(F::half(F::sub(yk, ym))));  // (yk - ym) / (2 i)
   }
 }
 
 // ---------------------------------------------------------------- forward z-pass (truncate, scale)
-__global__ void k_fft_z_fwd(FFTPlan pl, Grid g, const cd* T, size_t tstride, FieldsW out, double scale) {
-  extern __shared__ cd sm[];
+template <class C>
+__global__ void k_fft_z_fwd(FFTPlan pl, Grid g, const C* T, size_t tstride, FieldsW out) {
+  using F = FT<C>;
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  C* sm = reinterpret_cast<C*>(sm_raw);
   const int batch = pl.batch, ld = pl.n + 1, pz = g.pz, nz = g.nz, h = g.nx / 2;
   const int kx0 = blockIdx.x * batch, j = blockIdx.y, f = blockIdx.z;
-  cd* a = sm;
-  cd* b = sm + batch * ld;
-  const cd* src = T + f * tstride + (size_t)j * pz * h;
+  C* a = sm;
+  C* b = sm + batch * ld;
+  const C* src = T + f * tstride + (size_t)j * pz * h;
   for (int idx = threadIdx.x; idx < pz * batch; idx += blockDim.x) {
     const int zz = idx / batch, bb = idx - zz * batch, kx = kx0 + bb;
-    a[bb * ld + zz] = kx < h ? src[(size_t)zz * h + kx] : mk(0, 0);
+    a[bb * ld + zz] = kx < h ? src[(size_t)zz * h + kx] : F::zero();
   }
   __syncthreads();
-  const cd* res = fft_batch<-1>(a, b, pl, batch, ld);
+  const C* res = fft_batch<C, -1>(a, b, pl, batch, ld);
   cd* dst = out.p[f] + (size_t)j * g.M;
   for (int idx = threadIdx.x; idx < nz * batch; idx += blockDim.x) {
     const int jz = idx / batch, bb = idx - jz * batch, kx = kx0 + bb;
     if (kx > h) continue;
     cd v = mk(0, 0);
-    if (kx < h && jz != nz / 2) v = scale * res[bb * ld + (jz < nz / 2 ? jz : pz - nz + jz)];
+    if (kx < h && jz != nz / 2) v = F::to_spec(res[bb * ld + (jz < nz / 2 ? jz : pz - nz + jz)], pl);
     dst[(size_t)jz * g.nxh + kx] = v;
   }
 }
@@ -228,8 +311,26 @@ static bool make_plan(int n, FFTPlan& p) {
 
 static size_t smem_bytes(const FFTPlan& p) { return (size_t)2 * p.batch * (p.n + 1) * sizeof(cd); }
 
+static df host_split(long double x) {
+  const float h = (float)x;
+  return df{h, (float)(x - (long double)h)};
+}
+
+template <class C>
+static int set_smem(const FFTPlan& fx, const FFTPlan& fz) {
+  const int sx = (int)smem_bytes(fx), sz = (int)smem_bytes(fz);
+  if (cudaFuncSetAttribute(k_fft_z_inv<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, sz) != cudaSuccess ||
+      cudaFuncSetAttribute(k_fft_z_fwd<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, sz) != cudaSuccess ||
+      cudaFuncSetAttribute(k_fft_x_inv<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, sx) != cudaSuccess ||
+      cudaFuncSetAttribute(k_fft_x_fwd<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, sx) != cudaSuccess)
+    return LMVD_ERR_CUDA;
+  return LMVD_OK;
+}
+
 int fft_prepare(Ctx& c) {
   if (!make_plan(c.g.px, c.fx) || !make_plan(c.g.pz, c.fz)) return LMVD_ERR_UNSUPPORTED;
+  const long double scale = 1.0L / ((long double)c.g.px * (long double)c.g.pz);
+  const long double pi = 3.141592653589793238462643383279502884L;
   for (FFTPlan* p : {&c.fx, &c.fz}) {
     const size_t per = (size_t)2 * (p->n + 1) * sizeof(cd);
     int b = (int)(98304 / per);
@@ -238,31 +339,39 @@ int fft_prepare(Ctx& c) {
     p->batch = b;
     if (smem_bytes(*p) > 200 * 1024) return LMVD_ERR_UNSUPPORTED;
     std::vector<double2> tw(p->n);
+    std::vector<float4> twf(p->n);
     for (int m = 0; m < p->n; ++m) {
-      const long double ang = 2.0L * 3.141592653589793238462643383279502884L * (long double)m / (long double)p->n;
-      tw[m] = make_double2((double)cosl(ang), (double)sinl(ang));
+      const long double ang = 2.0L * pi * (long double)m / (long double)p->n;
+      const long double cs = cosl(ang), sn = sinl(ang);
+      tw[m] = make_double2((double)cs, (double)sn);
+      const df hc = host_split(cs), hs = host_split(sn);
+      twf[m] = make_float4(hc.hi, hc.lo, hs.hi, hs.lo);
     }
     if (cudaMalloc(&p->tw, sizeof(double2) * p->n) != cudaSuccess) return LMVD_ERR_OOM;
     c.small_allocs.push_back(p->tw);
-    if (cudaMemcpy(p->tw, tw.data(), sizeof(double2) * p->n, cudaMemcpyHostToDevice) != cudaSuccess)
+    if (cudaMalloc(&p->twf, sizeof(float4) * p->n) != cudaSuccess) return LMVD_ERR_OOM;
+    c.small_allocs.push_back(p->twf);
+    if (cudaMemcpy(p->tw, tw.data(), sizeof(double2) * p->n, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(p->twf, twf.data(), sizeof(float4) * p->n, cudaMemcpyHostToDevice) != cudaSuccess)
       return LMVD_ERR_CUDA;
+    p->scale_d = (double)scale;
+    p->scale_f = host_split(scale);
+    p->s3f = host_split(sqrtl(3.0L) / 2.0L);
   }
-  const int sx = (int)smem_bytes(c.fx), sz = (int)smem_bytes(c.fz);
-  if (cudaFuncSetAttribute(k_fft_z_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, sz) != cudaSuccess ||
-      cudaFuncSetAttribute(k_fft_z_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, sz) != cudaSuccess ||
-      cudaFuncSetAttribute(k_fft_x_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, sx) != cudaSuccess ||
-      cudaFuncSetAttribute(k_fft_x_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, sx) != cudaSuccess)
-    return LMVD_ERR_CUDA;
-  return LMVD_OK;
+  int e = set_smem<cd>(c.fx, c.fz);
+  if (!e) e = set_smem<cdf>(c.fx, c.fz);
+  return e;
 }
 
 static inline unsigned cdiv(unsigned a, unsigned b) { return (a + b - 1) / b; }
 // conventional algorithmic flop count of one complex transform of length n: 5 n log2 n
 static inline double fft_flops(double n) { return 5.0 * n * std::log2(n); }
 
-void fft_inverse(Ctx& c, cd* const* in, double* const* out, int nf) {
+template <class C>
+static void inverse_t(Ctx& c, cd* const* in, void* const* out, int nf) {
   const Grid& g = c.g;
   const size_t tstride = (size_t)g.ny * g.pz * (g.nx / 2);
+  C* T = reinterpret_cast<C*>(c.tbuf);
   for (int f0 = 0; f0 < nf; f0 += 10) {
     const int n = nf - f0 < 10 ? nf - f0 : 10;
     FieldsC fi{};
@@ -273,18 +382,19 @@ void fft_inverse(Ctx& c, cd* const* in, double* const* out, int nf) {
     }
     const double h = g.nx / 2, ny = g.ny, pz = g.pz, px = g.px;
     dim3 gz(cdiv(g.nx / 2, c.fz.batch), g.ny, n);
-    LMVD_LAUNCH(c, KC_FFT_Z_INV, n * ny * h * fft_flops(pz), n * ny * h * 16.0 * ((g.nz - 1) + pz), k_fft_z_inv, gz,
-                256, smem_bytes(c.fz), c.fz, g, fi, c.tbuf, tstride);
+    LMVD_LAUNCH(c, KC_FFT_Z_INV, n * ny * h * fft_flops(pz), n * ny * h * 16.0 * ((g.nz - 1) + pz), k_fft_z_inv<C>,
+                gz, 256, smem_bytes(c.fz), c.fz, g, fi, T, tstride);
     dim3 gx(cdiv(cdiv(g.pz, 2), c.fx.batch), g.ny, n);
     LMVD_LAUNCH(c, KC_FFT_X_INV, n * ny * ((g.pz + 1) / 2) * fft_flops(px), n * ny * pz * (16.0 * h + 8.0 * px),
-                k_fft_x_inv, gx, 256, smem_bytes(c.fx), c.fx, g, c.tbuf, tstride, fo);
+                k_fft_x_inv<C>, gx, 256, smem_bytes(c.fx), c.fx, g, T, tstride, fo);
   }
 }
 
-void fft_forward(Ctx& c, double* const* in, cd* const* out, int nf) {
+template <class C>
+static void forward_t(Ctx& c, void* const* in, cd* const* out, int nf) {
   const Grid& g = c.g;
   const size_t tstride = (size_t)g.ny * g.pz * (g.nx / 2);
-  const double scale = 1.0 / ((double)g.px * (double)g.pz);
+  C* T = reinterpret_cast<C*>(c.tbuf);
   for (int f0 = 0; f0 < nf; f0 += 10) {
     const int n = nf - f0 < 10 ? nf - f0 : 10;
     FieldsRC fi{};
@@ -296,11 +406,25 @@ void fft_forward(Ctx& c, double* const* in, cd* const* out, int nf) {
     const double h = g.nx / 2, ny = g.ny, pz = g.pz, px = g.px;
     dim3 gx(cdiv(cdiv(g.pz, 2), c.fx.batch), g.ny, n);
     LMVD_LAUNCH(c, KC_FFT_X_FWD, n * ny * ((g.pz + 1) / 2) * fft_flops(px), n * ny * pz * (16.0 * h + 8.0 * px),
-                k_fft_x_fwd, gx, 256, smem_bytes(c.fx), c.fx, g, fi, c.tbuf, tstride);
+                k_fft_x_fwd<C>, gx, 256, smem_bytes(c.fx), c.fx, g, fi, T, tstride);
     dim3 gz(cdiv(g.nx / 2 + 1, c.fz.batch), g.ny, n);
     LMVD_LAUNCH(c, KC_FFT_Z_FWD, n * ny * h * fft_flops(pz), n * ny * 16.0 * (pz * h + (double)g.nz * g.nxh),
-                k_fft_z_fwd, gz, 256, smem_bytes(c.fz), c.fz, g, c.tbuf, tstride, fo, scale);
+                k_fft_z_fwd<C>, gz, 256, smem_bytes(c.fz), c.fz, g, T, tstride, fo);
   }
+}
+
+void fft_inverse(Ctx& c, cd* const* in, double* const* out, int nf) {
+  void* o[64];
+  for (int f = 0; f < nf; ++f) o[f] = out[f];
+  if (c.cfg.precision == 1) inverse_t<cdf>(c, in, o, nf);
+  else inverse_t<cd>(c, in, o, nf);
+}
+
+void fft_forward(Ctx& c, double* const* in, cd* const* out, int nf) {
+  void* i[64];
+  for (int f = 0; f < nf; ++f) i[f] = in[f];
+  if (c.cfg.precision == 1) forward_t<cdf>(c, i, out, nf);
+  else forward_t<cd>(c, i, out, nf);
 }
 
 }  // namespace lmvd

@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "../../include/lmvd.h"
+#include "df64.h"
 
 namespace lmvd {
 
@@ -79,7 +80,11 @@ struct FFTPlan {
   int nst = 0;
   int radix[24];
   double2* tw = nullptr;   // tw[m] = (cos 2 pi m / n, sin 2 pi m / n), device
+  float4* twf = nullptr;   // the same as double-float pairs (cos.hi, cos.lo, sin.hi, sin.lo), device
   int batch = 1;           // transforms per CTA
+  double scale_d = 1.0;    // 1 / (px pz) for the forward z-pass
+  df scale_f{1.f, 0.f};
+  df s3f{0.f, 0.f};        // sin(2 pi / 3) as a double-float
 };
 
 // ---------------------------------------------------------------- per-class launch accounting

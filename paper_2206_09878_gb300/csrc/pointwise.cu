@@ -63,3 +63,68 @@ __global__ void k_products_p2(size_t n, const double* md1, const double* md2, co
 }
 
 }  // namespace lmvd
+
+// ------------------------------------------------------------------ double-float variants (precision 1)
+namespace lmvd {
+
+__device__ __forceinline__ df ld(const double* p, size_t o) { return reinterpret_cast<const df*>(p)[o]; }
+__device__ __forceinline__ void st(double* p, size_t o, df v) { reinterpret_cast<df*>(p)[o] = v; }
+
+__global__ void k_products_p1_df(size_t n, EosArgs e, const double* zp, const double* zx, const double* zz,
+                                 const double* zy, const double* lapz, const double* m1, const double* m2,
+                                 const double* m3, double* rho, double* invrho, double* fprime, double* w1,
+                                 double* w2, double* w3, double* rz) {
+  const df rh = df_from_double(e.rh);
+  const df drho = df_from_double(e.rh - e.rl);
+  const df irlrh = df_from_double(1.0 / (e.rl * e.rh));
+  const df cfp = df_from_double((e.rh - e.rl) / (e.rl * e.rh));
+  const df kap = df_from_double(e.kappa);
+  for (size_t o = blockIdx.x * (size_t)blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x) {
+    const df ir = dmul(dsub(rh, dmul(drho, ld(zp, o))), irlrh);
+    const df r = drcp(ir);
+    const df gx = ld(zx, o), gy = ld(zy, o), gz = ld(zz, o);
+    st(rho, o, r);
+    st(invrho, o, ir);
+    st(fprime, o, dmul(dmul(r, r), cfp));
+    st(w1, o, dmul(gx, ir));
+    st(w2, o, dmul(gy, ir));
+    st(w3, o, dmul(gz, ir));
+    const df adv = dadd(ddot2(ld(m1, o), gx, ld(m2, o), gy), dmul(ld(m3, o), gz));
+    st(rz, o, dmul(dsub(dmul(kap, ld(lapz, o)), adv), ir));
+  }
+}
+
+__global__ void k_product_rt_df(size_t n, const double* fprime, const double* zdot, double* out) {
+  for (size_t o = blockIdx.x * (size_t)blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x)
+    st(out, o, dmul(ld(fprime, o), ld(zdot, o)));
+}
+
+__global__ void k_product_L_df(size_t n, const double* w1, const double* w2, const double* w3, const double* m1,
+                               const double* m2, const double* m3, double* out) {
+  for (size_t o = blockIdx.x * (size_t)blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x) {
+    const df s = dadd(ddot2(ld(w1, o), ld(m1, o), ld(w2, o), ld(m2, o)), dmul(ld(w3, o), ld(m3, o)));
+    st(out, o, dneg(s));
+  }
+}
+
+__global__ void k_products_p2_df(size_t n, const double* md1, const double* md2, const double* md3,
+                                 const double* mc1, const double* mc2, const double* mc3, const double* rho,
+                                 const double* invrho, P2Out q) {
+  for (size_t o = blockIdx.x * (size_t)blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x) {
+    const df ir = ld(invrho, o);
+    const df a = dadd(ld(md1, o), ld(mc1, o)), b = dadd(ld(md2, o), ld(mc2, o)), c = dadd(ld(md3, o), ld(mc3, o));
+    const df ua = dmul(a, ir), ub = dmul(b, ir), uc = dmul(c, ir);
+    st(q.p[0], o, dneg(dmul(a, ua)));
+    st(q.p[1], o, dneg(dmul(a, ub)));
+    st(q.p[2], o, dneg(dmul(a, uc)));
+    st(q.p[3], o, dneg(dmul(b, ub)));
+    st(q.p[4], o, dneg(dmul(b, uc)));
+    st(q.p[5], o, dneg(dmul(c, uc)));
+    st(q.p[6], o, ua);
+    st(q.p[7], o, ub);
+    st(q.p[8], o, uc);
+    st(q.p[9], o, ld(rho, o));
+  }
+}
+
+}  // namespace lmvd

@@ -77,4 +77,16 @@ struct P2Out {
 __global__ void k_products_p2(size_t n, const double* md1, const double* md2, const double* md3, const double* mc1,
                               const double* mc2, const double* mc3, const double* rho, const double* invrho, P2Out o);
 
+// double-float variants (physical fields hold hi/lo float pairs in the same storage)
+__global__ void k_products_p1_df(size_t n, EosArgs e, const double* zp, const double* zx, const double* zz,
+                                 const double* zy, const double* lapz, const double* m1, const double* m2,
+                                 const double* m3, double* rho, double* invrho, double* fprime, double* w1,
+                                 double* w2, double* w3, double* rz);
+__global__ void k_product_rt_df(size_t n, const double* fprime, const double* zdot, double* out);
+__global__ void k_product_L_df(size_t n, const double* w1, const double* w2, const double* w3, const double* m1,
+                               const double* m2, const double* m3, double* out);
+__global__ void k_products_p2_df(size_t n, const double* md1, const double* md2, const double* md3,
+                                 const double* mc1, const double* mc2, const double* mc3, const double* rho,
+                                 const double* invrho, P2Out o);
+
 }  // namespace lmvd

@@ -19,11 +19,11 @@ def oracle_config(w, **over):
     return Config(**c)
 
 
-def gpu_config(L, cfg):
+def gpu_config(L, cfg, precision=0):
     return L.lmvd_default_config(cfg.nx, cfg.ny, cfg.nz, spline_order=cfg.p, lx=cfg.lx, lz=cfg.lz, y0=cfg.y0,
                                  y1=cfg.y1, re=cfg.re, sc=cfg.sc, fr=cfg.fr, rho_heavy=cfg.rho_h,
                                  rho_light=cfg.rho_l, dt=cfg.dt, kf=cfg.kf, beta_n=cfg.beta_n,
-                                 beta_p=cfg.beta_p, n_startup=cfg.n_startup)
+                                 beta_p=cfg.beta_p, n_startup=cfg.n_startup, precision=precision)
 
 
 def to_torch(st, device="cuda"):
@@ -54,10 +54,10 @@ def compare_states(S, gpu, ora):
     return e
 
 
-def make_pair(L, name, **over):
+def make_pair(L, name, precision=0, **over):
     w = workload(name, **{k: v for k, v in over.items() if k in WORKLOADS[name]})
     cfg = oracle_config(w, **{k: v for k, v in over.items() if k not in WORKLOADS[name]})
     S = Substage(cfg)
     st = rt_state(**w)
-    ctx = L.Context(gpu_config(L, cfg))
+    ctx = L.Context(gpu_config(L, cfg, precision))
     return S, ctx, st, cfg

@@ -35,12 +35,12 @@ def test_every_declared_symbol_is_exported(lib):
 def test_config_struct_layout_matches(lib):
     cfg = lib.lmvd_default_config(32, 33, 32)
     assert ctypes.sizeof(cfg) == 128
-    assert (cfg.spline_order, cfg.kf, cfg.n_startup) == (6, 4, 20)
+    assert (cfg.spline_order, cfg.kf, cfg.n_startup, cfg.precision) == (6, 4, 20, 0)
     assert cfg.beta_n == 0.0 and cfg.beta_p == -4.0 and abs(cfg.rho_light - 1 / 3) < 1e-16
 
 
 @pytest.mark.parametrize("bad", [dict(nx=7), dict(ny=5), dict(spline_order=3), dict(dt=0.0), dict(re=-1.0),
-                                 dict(y1=-2.0), dict(kf=-1)])
+                                 dict(y1=-2.0), dict(kf=-1), dict(precision=2)])
 def test_invalid_configs_rejected_without_gpu(lib, bad):
     cfg = lib.lmvd_default_config(32, 33, 32)
     for k, v in bad.items():

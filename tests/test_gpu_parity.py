@@ -38,14 +38,16 @@ def _field_errors(L, S, ctx):
     return out
 
 
+@pytest.mark.parametrize("precision", [0, 1])
 @pytest.mark.parametrize("name,over", [
     ("rt32", {}),
     ("rt32", dict(nx=24, ny=21, nz=16, kmax=3)),
     ("rt32", dict(p=4, ny=25)),
 ])
-def test_substages_match_oracle(L, name, over):
+def test_substages_match_oracle(L, name, over, precision):
+    """precision 0: FP64 throughout; 1: double-float transforms and products, FP64 spectral steps."""
     from _pairs import compare_states, make_pair, to_numpy, to_torch
-    S, ctx, st, cfg = make_pair(L, name, **over)
+    S, ctx, st, cfg = make_pair(L, name, precision=precision, **over)
     S.set_state(**st)
     ctx.set_state(to_torch(st))
     nsub = 2 * 5 if not over else 4
@@ -64,10 +66,11 @@ def test_substages_match_oracle(L, name, over):
     assert all(v <= TOL for v in worst.values()), worst
 
 
-def test_constant_density_and_flat_interface(L):
+@pytest.mark.parametrize("precision", [0, 1])
+def test_constant_density_and_flat_interface(L, precision):
     """Degenerate cases: rho_h = rho_l (f' = 0, m^c = 0) and a state at rest with a flat interface."""
     from _pairs import compare_states, make_pair, to_numpy, to_torch
-    S, ctx, st, cfg = make_pair(L, "rt32", ratio=1.0 + 1e-12, eta_rms=0.0, u_rms=0.0)
+    S, ctx, st, cfg = make_pair(L, "rt32", precision=precision, ratio=1.0 + 1e-12, eta_rms=0.0, u_rms=0.0)
     S.set_state(**st)
     ctx.set_state(to_torch(st))
     for _ in range(2):
@@ -80,10 +83,11 @@ def test_constant_density_and_flat_interface(L):
     ctx.close()
 
 
-def test_restart_from_history_is_bitwise(L):
+@pytest.mark.parametrize("precision", [0, 1])
+def test_restart_from_history_is_bitwise(L, precision):
     """get_state(history) -> set_state(history) resumes the same sequence bit for bit."""
     from _pairs import make_pair, to_numpy, to_torch
-    S, ctx, st, cfg = make_pair(L, "rt32")
+    S, ctx, st, cfg = make_pair(L, "rt32", precision=precision)
     ctx.set_state(to_torch(st))
     ctx.advance_substage()
     hist = ctx.history_buffer()
