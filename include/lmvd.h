@@ -135,6 +135,21 @@ int lmvd_step(lmvd_ctx* ctx, int nsteps);
 int lmvd_get_field(lmvd_ctx* ctx, int which, void* out);
 size_t lmvd_field_bytes(const lmvd_ctx* ctx, int which);
 
+/* Fourier synthesis / analysis with the 3/2 rule (Eq. disc_f; Sec. 4.4: nonlinear terms are formed
+ * on the physical grid), always in FP64, on the context's grid and stream, using its workspace.
+ * spec: nfields consecutive spectral arrays [ny][nz][nx/2+1] complex128 holding values at the ny
+ *       collocation points (not B-spline coefficients); Nyquist slots are ignored on input and
+ *       written as zero on output.
+ * phys: nfields consecutive physical arrays [ny][3nz/2][3nx/2] float64 on the padded grid
+ *       x_i = i lx / (3nx/2), z_k = k lz / (3nz/2).
+ * lmvd_inverse_transform: phys(x, z) = sum over retained (kx, kz) of spec exp(i (kx x + kz z)),
+ *   the kx < 0 half by Hermitian symmetry (the kx = 0 column is taken as Hermitian).
+ * lmvd_forward_transform: spec = retained coefficients of phys, scaled by 1 / ((3nx/2)(3nz/2)).
+ * Both pointers must be device memory owned by the caller. Asynchronous.
+ * Errors: INVALID_ARG (NULL pointer, nfields < 0), CUDA. */
+int lmvd_inverse_transform(lmvd_ctx* ctx, const void* spec, double* phys, int nfields);
+int lmvd_forward_transform(lmvd_ctx* ctx, const double* phys, void* spec, int nfields);
+
 /* Substage counter s (0 after a start-up). -1 if ctx is NULL. */
 int lmvd_substage_index(const lmvd_ctx* ctx);
 

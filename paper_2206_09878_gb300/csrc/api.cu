@@ -712,6 +712,40 @@ int lmvd_get_field(lmvd_ctx* h, int which, void* out) {
   return e ? latch(c, e) : LMVD_OK;
 }
 
+int lmvd_inverse_transform(lmvd_ctx* h, const void* spec, double* phys, int nfields) {
+  if (!h || !spec || !phys || nfields < 0) return LMVD_ERR_INVALID_ARG;
+  Ctx& c = h->c;
+  const size_t S = (size_t)c.g.ny * c.g.M, P = (size_t)c.g.ny * c.g.P;
+  for (int f0 = 0; f0 < nfields; f0 += 10) {
+    const int n = std::min(10, nfields - f0);
+    cd* in[10];
+    double* out[10];
+    for (int f = 0; f < n; ++f) {
+      in[f] = (cd*)spec + (size_t)(f0 + f) * S;
+      out[f] = phys + (size_t)(f0 + f) * P;
+    }
+    fft_inverse_as(c, in, out, n, 0);
+  }
+  return cuda_check(c);
+}
+
+int lmvd_forward_transform(lmvd_ctx* h, const double* phys, void* spec, int nfields) {
+  if (!h || !spec || !phys || nfields < 0) return LMVD_ERR_INVALID_ARG;
+  Ctx& c = h->c;
+  const size_t S = (size_t)c.g.ny * c.g.M, P = (size_t)c.g.ny * c.g.P;
+  for (int f0 = 0; f0 < nfields; f0 += 10) {
+    const int n = std::min(10, nfields - f0);
+    double* in[10];
+    cd* out[10];
+    for (int f = 0; f < n; ++f) {
+      in[f] = (double*)phys + (size_t)(f0 + f) * P;
+      out[f] = (cd*)spec + (size_t)(f0 + f) * S;
+    }
+    fft_forward_as(c, in, out, n, 0);
+  }
+  return cuda_check(c);
+}
+
 int lmvd_substage_index(const lmvd_ctx* h) { return h ? h->c.s : -1; }
 
 int lmvd_synchronize(lmvd_ctx* h) {

@@ -413,18 +413,22 @@ static void forward_t(Ctx& c, void* const* in, cd* const* out, int nf) {
   }
 }
 
-void fft_inverse(Ctx& c, cd* const* in, double* const* out, int nf) {
+void fft_inverse_as(Ctx& c, cd* const* in, double* const* out, int nf, int precision) {
   void* o[64];
   for (int f = 0; f < nf; ++f) o[f] = out[f];
-  if (c.cfg.precision == 1) inverse_t<cdf>(c, in, o, nf);
+  if (precision == 1) inverse_t<cdf>(c, in, o, nf);
   else inverse_t<cd>(c, in, o, nf);
 }
 
-void fft_forward(Ctx& c, double* const* in, cd* const* out, int nf) {
+void fft_forward_as(Ctx& c, double* const* in, cd* const* out, int nf, int precision) {
   void* i[64];
   for (int f = 0; f < nf; ++f) i[f] = in[f];
-  if (c.cfg.precision == 1) forward_t<cdf>(c, i, out, nf);
+  if (precision == 1) forward_t<cdf>(c, i, out, nf);
   else forward_t<cd>(c, i, out, nf);
 }
+
+void fft_inverse(Ctx& c, cd* const* in, double* const* out, int nf) { fft_inverse_as(c, in, out, nf, c.cfg.precision); }
+
+void fft_forward(Ctx& c, double* const* in, cd* const* out, int nf) { fft_forward_as(c, in, out, nf, c.cfg.precision); }
 
 }  // namespace lmvd

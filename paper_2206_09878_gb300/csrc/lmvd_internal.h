@@ -163,5 +163,8 @@ int fft_prepare(Ctx& c);                       // plans, twiddles, smem attribut
 void fft_inverse(Ctx& c, cd* const* in, double* const* out, int nf);
 // forward: nf physical fields -> spectral value fields, truncated and scaled
 void fft_forward(Ctx& c, double* const* in, cd* const* out, int nf);
+// the same with an explicit arithmetic (0: complex double, 1: double-float), nf <= 64
+void fft_inverse_as(Ctx& c, cd* const* in, double* const* out, int nf, int precision);
+void fft_forward_as(Ctx& c, double* const* in, cd* const* out, int nf, int precision);
 
 }  // namespace lmvd

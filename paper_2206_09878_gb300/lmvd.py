@@ -63,6 +63,8 @@ def _load():
         "lmvd_profile_read": (I, [P, I, ctypes.POINTER(ctypes.c_double)]),
         "lmvd_kernel_class_name": (ctypes.c_char_p, [I]),
         "lmvd_kernel_launches": (ctypes.c_longlong, [P]),
+        "lmvd_inverse_transform": (I, [P, P, P, I]),
+        "lmvd_forward_transform": (I, [P, P, P, I]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -77,7 +79,8 @@ _lib = _load()
 EXPORTED = ("lmvd_default_config", "lmvd_create", "lmvd_destroy", "lmvd_set_state", "lmvd_get_state",
             "lmvd_history_bytes", "lmvd_advance_substage", "lmvd_step", "lmvd_get_field", "lmvd_field_bytes",
             "lmvd_substage_index", "lmvd_synchronize", "lmvd_status", "lmvd_strerror", "lmvd_profile_enable",
-            "lmvd_profile_read", "lmvd_kernel_class_name", "lmvd_kernel_launches")
+            "lmvd_profile_read", "lmvd_kernel_class_name", "lmvd_kernel_launches", "lmvd_inverse_transform",
+            "lmvd_forward_transform")
 LMVD_KERNEL_CLASSES = 13
 
 
@@ -181,6 +184,14 @@ def lmvd_kernel_class_name(cls):
 
 def lmvd_kernel_launches(h):
     return int(_lib.lmvd_kernel_launches(h))
+
+
+def lmvd_inverse_transform(h, spec, phys, nfields):
+    _check(_lib.lmvd_inverse_transform(h, _ptr(spec), _ptr(phys), int(nfields)), "lmvd_inverse_transform")
+
+
+def lmvd_forward_transform(h, phys, spec, nfields):
+    _check(_lib.lmvd_forward_transform(h, _ptr(phys), _ptr(spec), int(nfields)), "lmvd_forward_transform")
 
 
 # ---------------------------------------------------------------- convenience (still marshalling only)
