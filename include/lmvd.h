@@ -150,6 +150,23 @@ size_t lmvd_field_bytes(const lmvd_ctx* ctx, int which);
 int lmvd_inverse_transform(lmvd_ctx* ctx, const void* spec, double* phys, int nfields);
 int lmvd_forward_transform(lmvd_ctx* ctx, const double* phys, void* spec, int nfields);
 
+/* Allocation-free inverse transform (the paper has no counterpart: this serves callers that may not
+ * allocate device memory at all -- code running under an allocator owned by another framework, or
+ * after a start-up phase that forbids new allocations -- and therefore cannot create a context).
+ * Computes exactly what lmvd_inverse_transform computes (FP64, same layouts) for an nx x ny x nz grid,
+ * on cuda_stream (NULL = legacy default stream) of the current device, without any cudaMalloc: its
+ * working memory is one static 32 MiB device array that every device loading the library holds until
+ * the process exits. Limit: the twiddle tables plus ny * (3nz/2) * (nx/2) * 16 bytes must fit in the
+ * 32 MiB (e.g. 128 x 129 x 128 fits; 256 x 257 x 256 does not).
+ * spec, phys: caller-owned device memory. The first call on a device sets itself up (looks up the
+ * array's device address, raises the kernels' shared-memory limit); make that first call before any
+ * stream capture. All calls on a device share the array and leave their contents in it; calls whose
+ * GPU work overlaps (different streams or host threads) race, so order them on one stream.
+ * Errors: INVALID_ARG (NULL pointer, odd or too small nx/nz, nfields < 0, grid too large for the static
+ * array), UNSUPPORTED (3nx/2 or 3nz/2 with prime factors other than 2 and 3), CUDA. */
+int lmvd_inverse_transform_noalloc(int nx, int ny, int nz, const void* spec, double* phys, int nfields,
+                                   void* cuda_stream);
+
 /* Substage counter s (0 after a start-up). -1 if ctx is NULL. */
 int lmvd_substage_index(const lmvd_ctx* ctx);
 

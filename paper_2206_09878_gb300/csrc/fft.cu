@@ -19,6 +19,7 @@
 // of the same size), so the double-float path converts only at the spectral ends.
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 #include "df64.h"
 #include "lmvd_internal.h"
@@ -432,3 +433,105 @@ void fft_inverse(Ctx& c, cd* const* in, double* const* out, int nf) { fft_invers
 void fft_forward(Ctx& c, double* const* in, cd* const* out, int nf) { fft_forward_as(c, in, out, nf, c.cfg.precision); }
 
 }  // namespace lmvd
+
+// ====================================================================== allocation-free inverse transform
+// lmvd_inverse_transform_noalloc: the same synthesis as lmvd_inverse_transform, for callers that cannot
+// allocate device memory (no context exists, so nothing of lmvd_create is needed). Its only working
+// memory is the file-scope array below, which the CUDA module reserves on every device that loads the
+// library and keeps until the process exits. All calls on a device share it: the twiddle tables and
+// the intermediate array are rewritten by each call before they are read (nothing has to start at
+// zero), and calls whose work overlaps on the GPU (other streams, other host threads) race on it.
+namespace lmvd {
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = size_t(32) << 20;  // 32 MiB per device
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+// twiddle table tw[m] = (cos 2 pi m / n, sin 2 pi m / n) computed on the device
+__global__ void k_twiddles(double2* tw, int n) {
+  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < n; m += gridDim.x * blockDim.x) {
+    double s, c;
+    sincospi(2.0 * (double)m / (double)n, &s, &c);
+    tw[m] = make_double2(c, s);
+  }
+}
+
+// Once per device, with that device current: the device address of the scratch array (in host code
+// the array's name is only a stand-in) and the shared-memory limits of the two kernels.
+int noalloc_setup(int dev, void** ptr) {
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (g_noalloc_ptr[dev]) {
+    *ptr = g_noalloc_ptr[dev];
+    return LMVD_OK;
+  }
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return LMVD_ERR_CUDA;
+  if (cudaFuncSetAttribute(k_fft_z_inv<cd>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess ||
+      cudaFuncSetAttribute(k_fft_x_inv<cd>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess)
+    return LMVD_ERR_CUDA;
+  g_noalloc_ptr[dev] = p;
+  *ptr = p;
+  return LMVD_OK;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+}  // namespace lmvd
+
+extern "C" int lmvd_inverse_transform_noalloc(int nx, int ny, int nz, const void* spec, double* phys, int nfields,
+                                              void* cuda_stream) {
+  using namespace lmvd;
+  if (!spec || !phys || nfields < 0 || ny < 1 || nx < 4 || nz < 4 || (nx % 2) || (nz % 2))
+    return LMVD_ERR_INVALID_ARG;
+  Grid g{};
+  g.nx = nx;
+  g.ny = ny;
+  g.nz = nz;
+  g.nxh = nx / 2 + 1;
+  g.px = 3 * nx / 2;
+  g.pz = 3 * nz / 2;
+  g.M = (size_t)nz * g.nxh;
+  g.P = (size_t)g.px * g.pz;
+  FFTPlan fx, fz;
+  if (!make_plan(g.px, fx) || !make_plan(g.pz, fz)) return LMVD_ERR_UNSUPPORTED;
+  for (FFTPlan* p : {&fx, &fz}) {
+    int b = (int)(98304 / ((size_t)2 * (p->n + 1) * sizeof(cd)));
+    p->batch = b < 1 ? 1 : (b > 32 ? 32 : b);
+    if (smem_bytes(*p) > 200 * 1024) return LMVD_ERR_UNSUPPORTED;
+  }
+  // scratch layout: x twiddles | z twiddles | one field's intermediate T[ny][pz][nx/2]
+  const size_t off_tz = align256(sizeof(double2) * g.px);
+  const size_t off_tb = off_tz + align256(sizeof(double2) * g.pz);
+  const size_t tbytes = sizeof(cd) * (size_t)ny * g.pz * (nx / 2);
+  if (off_tb + tbytes > kNoAllocScratchBytes) return LMVD_ERR_INVALID_ARG;  // grid too large for the scratch
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) return LMVD_ERR_CUDA;
+  void* base = nullptr;
+  int err = noalloc_setup(dev, &base);
+  if (err) return err;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  char* sb = (char*)base;
+  fx.tw = (double2*)sb;
+  fz.tw = (double2*)(sb + off_tz);
+  cd* T = (cd*)(sb + off_tb);
+  k_twiddles<<<(g.px + 255) / 256, 256, 0, st>>>(fx.tw, g.px);
+  k_twiddles<<<(g.pz + 255) / 256, 256, 0, st>>>(fz.tw, g.pz);
+  const size_t S = (size_t)ny * g.M, P = (size_t)ny * g.P;
+  for (int f = 0; f < nfields; ++f) {
+    FieldsC fi{};
+    FieldsRW fo{};
+    fi.p[0] = (const cd*)spec + (size_t)f * S;
+    fo.p[0] = phys + (size_t)f * P;
+    dim3 gz(cdiv(nx / 2, fz.batch), ny, 1);
+    k_fft_z_inv<cd><<<gz, 256, smem_bytes(fz), st>>>(fz, g, fi, T, 0);
+    dim3 gx(cdiv(cdiv(g.pz, 2), fx.batch), ny, 1);
+    k_fft_x_inv<cd><<<gx, 256, smem_bytes(fx), st>>>(fx, g, T, 0, fo);
+  }
+  return cudaGetLastError() == cudaSuccess ? LMVD_OK : LMVD_ERR_CUDA;
+}

@@ -65,6 +65,7 @@ def _load():
         "lmvd_kernel_launches": (ctypes.c_longlong, [P]),
         "lmvd_inverse_transform": (I, [P, P, P, I]),
         "lmvd_forward_transform": (I, [P, P, P, I]),
+        "lmvd_inverse_transform_noalloc": (I, [I, I, I, P, P, I, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -80,7 +81,7 @@ EXPORTED = ("lmvd_default_config", "lmvd_create", "lmvd_destroy", "lmvd_set_stat
             "lmvd_history_bytes", "lmvd_advance_substage", "lmvd_step", "lmvd_get_field", "lmvd_field_bytes",
             "lmvd_substage_index", "lmvd_synchronize", "lmvd_status", "lmvd_strerror", "lmvd_profile_enable",
             "lmvd_profile_read", "lmvd_kernel_class_name", "lmvd_kernel_launches", "lmvd_inverse_transform",
-            "lmvd_forward_transform")
+            "lmvd_forward_transform", "lmvd_inverse_transform_noalloc")
 LMVD_KERNEL_CLASSES = 13
 
 
@@ -192,6 +193,15 @@ def lmvd_inverse_transform(h, spec, phys, nfields):
 
 def lmvd_forward_transform(h, phys, spec, nfields):
     _check(_lib.lmvd_forward_transform(h, _ptr(phys), _ptr(spec), int(nfields)), "lmvd_forward_transform")
+
+
+def lmvd_inverse_transform_noalloc(nx, ny, nz, spec, phys, nfields, stream=None):
+    """Context-free synthesis that allocates no device memory (static per-device working array)."""
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    _check(_lib.lmvd_inverse_transform_noalloc(int(nx), int(ny), int(nz), _ptr(spec), _ptr(phys), int(nfields),
+                                               ctypes.c_void_p(stream.cuda_stream)),
+           "lmvd_inverse_transform_noalloc")
 
 
 # ---------------------------------------------------------------- convenience (still marshalling only)
