@@ -334,6 +334,9 @@ def run_cuda(args):
                           "FP64 solves / RHS / update"),
             "value": v2, "unit": UNIT, "ms_per_step": r2["ms"] / args.steps, "clocks": r2["clocks"],
             "roofline": roofline_of(r2["prof"], r2["ms"], other),
+            "kernels": {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps,
+                            "tflops": (v[2] / (v[0] / 1e3) / 1e12) if v[0] > 0 else None}
+                        for k, v in r2["prof"].items() if v[1] > 0},
             "state_rel_l2_vs_headline_after_%d_substages" % (args.warmup + args.steps): errs,
         }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

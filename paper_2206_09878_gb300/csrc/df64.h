@@ -27,6 +27,27 @@ __host__ __device__ inline df df_from_double(double x) {
 }
 __host__ __device__ inline double df_to_double(df a) { return (double)a.hi + (double)a.lo; }
 
+// Split of a double into hi + lo with integer operations only (no FP64 instruction): hi takes the
+// sign, exponent and the top 23 stored mantissa bits (truncation), lo the remaining 29 bits rounded
+// to 24 by one int-to-float conversion and scaled by a power of two; a FastTwoSum renormalises.
+// Relative error <= 2^-48. Magnitudes outside [2^-66, 2^127) (and 0, inf, nan) take the FP64 route.
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e);
+__device__ __forceinline__ df df_from_double_int(double x) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi32 = (unsigned)(u >> 32);
+  const int e = (int)((hi32 >> 20) & 0x7ffu);
+  if (e < 957 || e > 1150) return df_from_double(x);
+  const unsigned sign = hi32 & 0x80000000u;
+  const unsigned long long m52 = u & 0xFFFFFFFFFFFFFull;
+  const float hi = __uint_as_float(sign | ((unsigned)(e - 896) << 23) | (unsigned)(m52 >> 29));
+  const float scale = __uint_as_float((unsigned)(e - 948) << 23);  // 2^(e - 1075)
+  float lo = __fmul_rn(__uint2float_rn((unsigned)(m52 & 0x1FFFFFFFull)), scale);
+  lo = sign ? -lo : lo;
+  float s, l;
+  fast_two_sum(hi, lo, s, l);
+  return df{s, l};
+}
+
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   s = __fadd_rn(a, b);
   const float bb = __fsub_rn(s, a);

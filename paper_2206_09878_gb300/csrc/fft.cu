@@ -92,7 +92,7 @@ struct FT<cdf> {
     const df s = SIGN > 0 ? p.s3f : dneg(p.s3f);
     return cdf{dmul(v.re, s), dmul(v.im, s)};
   }
-  __device__ static cdf from_spec(cd x) { return cdf{df_from_double(x.re), df_from_double(x.im)}; }
+  __device__ static cdf from_spec(cd x) { return cdf{df_from_double_int(x.re), df_from_double_int(x.im)}; }
   __device__ static cd to_spec(cdf x, const FFTPlan& p) {
     return cd{df_to_double(dmul(x.re, p.scale_f)), df_to_double(dmul(x.im, p.scale_f))};
   }
@@ -102,80 +102,81 @@ struct FT<cdf> {
   __device__ static R rzero() { return df{0.f, 0.f}; }
 };
 
-// One Stockham stage set on a batch of transforms of length n stored with leading dimension ld.
-// SIGN = +1: synthesis (exp(+i)), -1: analysis. Returns the buffer holding the result.
-template <class C, int SIGN>
-__device__ C* fft_batch(C* a, C* b, const FFTPlan& pl, int batch, int ld) {
+// One radix-R Stockham stage, in place in shared memory. The transform of length n is shared by
+// tpt = n / EPT threads; thread tt owns the butterflies tt, tt + tpt, ... (EPT / R of them), loads all
+// their inputs into registers, waits for the whole block, then writes the outputs back to the same
+// buffer (the reads of every thread are complete before any write).
+template <class C, int SIGN, int R, int EPT>
+__device__ __forceinline__ void fft_stage(C* x, const FFTPlan& pl, int L, int tt, int tpt) {
   using F = FT<C>;
+  constexpr int NBT = EPT / R;
   const int n = pl.n;
-  C* in = a;
-  C* out = b;
+  const int nb = n / R, Ls = L * R, tws = n / Ls;
+  const bool pow2 = (L & (L - 1)) == 0;
+  C v[NBT][R];
+#pragma unroll
+  for (int j = 0; j < NBT; ++j) {
+    const int b = tt + j * tpt;
+#pragma unroll
+    for (int q = 0; q < R; ++q) v[j][q] = x[b + q * nb];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < NBT; ++j) {
+    const int b = tt + j * tpt;
+    const int k = pow2 ? (b & (L - 1)) : (b % L);
+    const int base = (b - k) * R + k;
+    if (k) {
+#pragma unroll
+      for (int q = 1; q < R; ++q) v[j][q] = F::template mulw<SIGN>(v[j][q], pl, q * k * tws);
+    }
+    if (R == 4) {
+      const C t0 = F::add(v[j][0], v[j][2]), t1 = F::sub(v[j][0], v[j][2]), t2 = F::add(v[j][1], v[j][3]);
+      const C d3 = F::ti(F::sub(v[j][1], v[j][3]));
+      const C t3 = SIGN > 0 ? d3 : F::neg(d3);  // (SIGN i) (v1 - v3)
+      x[base] = F::add(t0, t2);
+      x[base + L] = F::add(t1, t3);
+      x[base + 2 * L] = F::sub(t0, t2);
+      x[base + 3 * L] = F::sub(t1, t3);
+    } else if (R == 3) {
+      const C t1 = F::add(v[j][1], v[j][2]);
+      const C m = F::sub(v[j][0], F::half(t1));
+      const C u = F::ti(F::template mul_s3<SIGN>(F::sub(v[j][1], v[j][2]), pl));
+      x[base] = F::add(v[j][0], t1);
+      x[base + L] = F::add(m, u);
+      x[base + 2 * L] = F::sub(m, u);
+    } else {
+      x[base] = F::add(v[j][0], v[j][1]);
+      x[base + L] = F::sub(v[j][0], v[j][1]);
+    }
+  }
+  __syncthreads();
+}
+
+// All stages of one transform held at x (the caller has synchronised after filling x).
+// SIGN = +1: synthesis (exp(+i)), -1: analysis. The result is in natural order in x.
+template <class C, int SIGN, int EPT>
+__device__ void fft_inplace(C* x, const FFTPlan& pl, int tt, int tpt) {
   int L = 1;
   for (int s = 0; s < pl.nst; ++s) {
     const int r = pl.radix[s];
-    const int Ls = L * r;
-    const int nb = n / r;
-    const int tws = n / Ls;
-    for (int t = threadIdx.x; t < batch * nb; t += blockDim.x) {
-      const int bt = t / nb;
-      const int i = t - bt * nb;
-      const int k = i % L;
-      const C* src = in + bt * ld;
-      C* dst = out + bt * ld;
-      const int base = (i - k) * r + k;
-      if (r == 4) {
-        C v0 = src[i], v1 = src[i + nb], v2 = src[i + 2 * nb], v3 = src[i + 3 * nb];
-        if (k) {
-          v1 = F::template mulw<SIGN>(v1, pl, k * tws);
-          v2 = F::template mulw<SIGN>(v2, pl, 2 * k * tws);
-          v3 = F::template mulw<SIGN>(v3, pl, 3 * k * tws);
-        }
-        const C t0 = F::add(v0, v2), t1 = F::sub(v0, v2), t2 = F::add(v1, v3);
-        const C d3 = F::ti(F::sub(v1, v3));
-        const C t3 = SIGN > 0 ? d3 : F::neg(d3);  // (SIGN i) (v1 - v3)
-        dst[base] = F::add(t0, t2);
-        dst[base + L] = F::add(t1, t3);
-        dst[base + 2 * L] = F::sub(t0, t2);
-        dst[base + 3 * L] = F::sub(t1, t3);
-      } else if (r == 3) {
-        C v0 = src[i], v1 = src[i + nb], v2 = src[i + 2 * nb];
-        if (k) {
-          v1 = F::template mulw<SIGN>(v1, pl, k * tws);
-          v2 = F::template mulw<SIGN>(v2, pl, 2 * k * tws);
-        }
-        const C t1 = F::add(v1, v2);
-        const C m = F::sub(v0, F::half(t1));
-        const C u = F::ti(F::template mul_s3<SIGN>(F::sub(v1, v2), pl));
-        dst[base] = F::add(v0, t1);
-        dst[base + L] = F::add(m, u);
-        dst[base + 2 * L] = F::sub(m, u);
-      } else {
-        C v0 = src[i], v1 = src[i + nb];
-        if (k) v1 = F::template mulw<SIGN>(v1, pl, k * tws);
-        dst[base] = F::add(v0, v1);
-        dst[base + L] = F::sub(v0, v1);
-      }
-    }
-    __syncthreads();
-    C* tmp = in;
-    in = out;
-    out = tmp;
-    L = Ls;
+    if (r == 4) fft_stage<C, SIGN, 4, EPT>(x, pl, L, tt, tpt);
+    else if (r == 3) fft_stage<C, SIGN, 3, EPT>(x, pl, L, tt, tpt);
+    else fft_stage<C, SIGN, 2, EPT>(x, pl, L, tt, tpt);
+    L *= r;
   }
-  return in;
 }
 
 // ---------------------------------------------------------------- inverse z-pass
 // in: spectral value fields [ny][nz][nxh] (complex double); T: [f][ny][pz][nx/2] of C
-template <class C>
+template <class C, int EPT>
 __global__ void k_fft_z_inv(FFTPlan pl, Grid g, FieldsC in, C* T, size_t tstride) {
   using F = FT<C>;
   extern __shared__ __align__(16) unsigned char sm_raw[];
-  C* sm = reinterpret_cast<C*>(sm_raw);
+  C* a = reinterpret_cast<C*>(sm_raw);
   const int batch = pl.batch, ld = pl.n + 1, pz = g.pz, nz = g.nz, h = g.nx / 2;
   const int kx0 = blockIdx.x * batch, j = blockIdx.y, f = blockIdx.z;
-  C* a = sm;
-  C* b = sm + batch * ld;
+  const int bt = threadIdx.x / pl.tpt, tt = threadIdx.x - bt * pl.tpt;
   for (int idx = threadIdx.x; idx < batch * ld; idx += blockDim.x) a[idx] = F::zero();
   __syncthreads();
   const cd* src = in.p[f] + (size_t)j * g.M;
@@ -187,7 +188,8 @@ __global__ void k_fft_z_inv(FFTPlan pl, Grid g, FieldsC in, C* T, size_t tstride
     }
   }
   __syncthreads();
-  const C* res = fft_batch<C, 1>(a, b, pl, batch, ld);
+  fft_inplace<C, 1, EPT>(a + bt * ld, pl, tt, pl.tpt);
+  const C* res = a;
   C* dst = T + f * tstride + (size_t)j * pz * h;
   for (int idx = threadIdx.x; idx < pz * batch; idx += blockDim.x) {
     const int zz = idx / batch, bb = idx - zz * batch, kx = kx0 + bb;
@@ -196,16 +198,15 @@ __global__ void k_fft_z_inv(FFTPlan pl, Grid g, FieldsC in, C* T, size_t tstride
 }
 
 // ---------------------------------------------------------------- inverse x-pass (c2r, 2 rows per transform)
-template <class C>
+template <class C, int EPT>
 __global__ void k_fft_x_inv(FFTPlan pl, Grid g, const C* T, size_t tstride, FieldsRW out) {
   using F = FT<C>;
   using R = typename F::R;
   extern __shared__ __align__(16) unsigned char sm_raw[];
-  C* sm = reinterpret_cast<C*>(sm_raw);
+  C* a = reinterpret_cast<C*>(sm_raw);
   const int batch = pl.batch, ld = pl.n + 1, px = g.px, pz = g.pz, h = g.nx / 2;
   const int pr0 = blockIdx.x * batch, j = blockIdx.y, f = blockIdx.z;
-  C* a = sm;
-  C* b = sm + batch * ld;
+  const int bt = threadIdx.x / pl.tpt, tt = threadIdx.x - bt * pl.tpt;
   for (int idx = threadIdx.x; idx < batch * ld; idx += blockDim.x) a[idx] = F::zero();
   __syncthreads();
   const C* src = T + f * tstride + (size_t)j * pz * h;
@@ -224,7 +225,8 @@ __global__ void k_fft_x_inv(FFTPlan pl, Grid g, const C* T, size_t tstride, Fiel
     }
   }
   __syncthreads();
-  const C* res = fft_batch<C, 1>(a, b, pl, batch, ld);
+  fft_inplace<C, 1, EPT>(a + bt * ld, pl, tt, pl.tpt);
+  const C* res = a;
   R* dst = reinterpret_cast<R*>(out.p[f]) + (size_t)j * g.P;
   for (int idx = threadIdx.x; idx < batch * px; idx += blockDim.x) {
     const int bb = idx / px, x = idx - bb * px;
@@ -237,16 +239,15 @@ __global__ void k_fft_x_inv(FFTPlan pl, Grid g, const C* T, size_t tstride, Fiel
 }
 
 // ---------------------------------------------------------------- forward x-pass (r2c, 2 rows per transform)
-template <class C>
+template <class C, int EPT>
 __global__ void k_fft_x_fwd(FFTPlan pl, Grid g, FieldsRC in, C* T, size_t tstride) {
   using F = FT<C>;
   using R = typename F::R;
   extern __shared__ __align__(16) unsigned char sm_raw[];
-  C* sm = reinterpret_cast<C*>(sm_raw);
+  C* a = reinterpret_cast<C*>(sm_raw);
   const int batch = pl.batch, ld = pl.n + 1, px = g.px, pz = g.pz, h = g.nx / 2;
   const int pr0 = blockIdx.x * batch, j = blockIdx.y, f = blockIdx.z;
-  C* a = sm;
-  C* b = sm + batch * ld;
+  const int bt = threadIdx.x / pl.tpt, tt = threadIdx.x - bt * pl.tpt;
   const R* src = reinterpret_cast<const R*>(in.p[f]) + (size_t)j * g.P;
   for (int idx = threadIdx.x; idx < batch * px; idx += blockDim.x) {
     const int bb = idx / px, x = idx - bb * px;
@@ -259,7 +260,8 @@ __global__ void k_fft_x_fwd(FFTPlan pl, Grid g, FieldsRC in, C* T, size_t tstrid
     a[bb * ld + x] = F::make(va, vb);
   }
   __syncthreads();
-  const C* res = fft_batch<C, -1>(a, b, pl, batch, ld);
+  fft_inplace<C, -1, EPT>(a + bt * ld, pl, tt, pl.tpt);
+  const C* res = a;
   C* dst = T + f * tstride + (size_t)j * pz * h;
   for (int idx = threadIdx.x; idx < batch * h; idx += blockDim.x) {
     const int bb = idx / h, k = idx - bb * h;
@@ -273,22 +275,22 @@ __global__ void k_fft_x_fwd(FFTPlan pl, Grid g, FieldsRC in, C* T, size_t tstrid
 }
 
 // ---------------------------------------------------------------- forward z-pass (truncate, scale)
-template <class C>
+template <class C, int EPT>
 __global__ void k_fft_z_fwd(FFTPlan pl, Grid g, const C* T, size_t tstride, FieldsW out) {
   using F = FT<C>;
   extern __shared__ __align__(16) unsigned char sm_raw[];
-  C* sm = reinterpret_cast<C*>(sm_raw);
+  C* a = reinterpret_cast<C*>(sm_raw);
   const int batch = pl.batch, ld = pl.n + 1, pz = g.pz, nz = g.nz, h = g.nx / 2;
   const int kx0 = blockIdx.x * batch, j = blockIdx.y, f = blockIdx.z;
-  C* a = sm;
-  C* b = sm + batch * ld;
+  const int bt = threadIdx.x / pl.tpt, tt = threadIdx.x - bt * pl.tpt;
   const C* src = T + f * tstride + (size_t)j * pz * h;
   for (int idx = threadIdx.x; idx < pz * batch; idx += blockDim.x) {
     const int zz = idx / batch, bb = idx - zz * batch, kx = kx0 + bb;
     a[bb * ld + zz] = kx < h ? src[(size_t)zz * h + kx] : F::zero();
   }
   __syncthreads();
-  const C* res = fft_batch<C, -1>(a, b, pl, batch, ld);
+  fft_inplace<C, -1, EPT>(a + bt * ld, pl, tt, pl.tpt);
+  const C* res = a;
   cd* dst = out.p[f] + (size_t)j * g.M;
   for (int idx = threadIdx.x; idx < nz * batch; idx += blockDim.x) {
     const int jz = idx / batch, bb = idx - jz * batch, kx = kx0 + bb;
@@ -300,6 +302,9 @@ __global__ void k_fft_z_fwd(FFTPlan pl, Grid g, const C* T, size_t tstride, Fiel
 }
 
 // ---------------------------------------------------------------- host side
+// Radix order 4s, 2s, 3s: the sub-length L is a power of two in every radix-4/2 stage (mask arithmetic).
+// 12 elements per thread (6 when n has a single factor 2, hence no radix-4 stage); about 256 threads
+// per CTA; one shared buffer of batch transforms with leading dimension n + 1.
 static bool make_plan(int n, FFTPlan& p) {
   p.n = n;
   p.nst = 0;
@@ -307,25 +312,39 @@ static bool make_plan(int n, FFTPlan& p) {
   while (m % 4 == 0) { p.radix[p.nst++] = 4; m /= 4; }
   while (m % 2 == 0) { p.radix[p.nst++] = 2; m /= 2; }
   while (m % 3 == 0) { p.radix[p.nst++] = 3; m /= 3; }
-  return m == 1 && p.nst < 24;
+  if (m != 1 || p.nst >= 24) return false;
+  p.ept = (n % 12 == 0) ? 12 : ((n % 6 == 0) ? 6 : 0);
+  if (!p.ept) return false;
+  p.tpt = n / p.ept;
+  if (p.tpt > 1024) return false;
+  p.batch = 256 / p.tpt < 1 ? 1 : 256 / p.tpt;
+  return true;
 }
 
-static size_t smem_bytes(const FFTPlan& p) { return (size_t)2 * p.batch * (p.n + 1) * sizeof(cd); }
+static size_t smem_bytes(const FFTPlan& p) { return (size_t)p.batch * (p.n + 1) * sizeof(cd); }
+static unsigned threads(const FFTPlan& p) { return (unsigned)(p.batch * p.tpt); }
 
 static df host_split(long double x) {
   const float h = (float)x;
   return df{h, (float)(x - (long double)h)};
 }
 
+template <class C, int EPT>
+static int set_smem_e(int sx, int sz) {
+  if (cudaFuncSetAttribute(k_fft_z_inv<C, EPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, sz) != cudaSuccess ||
+      cudaFuncSetAttribute(k_fft_z_fwd<C, EPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, sz) != cudaSuccess ||
+      cudaFuncSetAttribute(k_fft_x_inv<C, EPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, sx) != cudaSuccess ||
+      cudaFuncSetAttribute(k_fft_x_fwd<C, EPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, sx) != cudaSuccess)
+    return LMVD_ERR_CUDA;
+  return LMVD_OK;
+}
+
 template <class C>
 static int set_smem(const FFTPlan& fx, const FFTPlan& fz) {
   const int sx = (int)smem_bytes(fx), sz = (int)smem_bytes(fz);
-  if (cudaFuncSetAttribute(k_fft_z_inv<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, sz) != cudaSuccess ||
-      cudaFuncSetAttribute(k_fft_z_fwd<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, sz) != cudaSuccess ||
-      cudaFuncSetAttribute(k_fft_x_inv<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, sx) != cudaSuccess ||
-      cudaFuncSetAttribute(k_fft_x_fwd<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, sx) != cudaSuccess)
-    return LMVD_ERR_CUDA;
-  return LMVD_OK;
+  int e = set_smem_e<C, 12>(sx, sz);
+  if (!e) e = set_smem_e<C, 6>(sx, sz);
+  return e;
 }
 
 int fft_prepare(Ctx& c) {
@@ -333,11 +352,6 @@ int fft_prepare(Ctx& c) {
   const long double scale = 1.0L / ((long double)c.g.px * (long double)c.g.pz);
   const long double pi = 3.141592653589793238462643383279502884L;
   for (FFTPlan* p : {&c.fx, &c.fz}) {
-    const size_t per = (size_t)2 * (p->n + 1) * sizeof(cd);
-    int b = (int)(98304 / per);
-    if (b < 1) b = 1;
-    if (b > 32) b = 32;
-    p->batch = b;
     if (smem_bytes(*p) > 200 * 1024) return LMVD_ERR_UNSUPPORTED;
     std::vector<double2> tw(p->n);
     std::vector<float4> twf(p->n);
@@ -383,11 +397,19 @@ static void inverse_t(Ctx& c, cd* const* in, void* const* out, int nf) {
     }
     const double h = g.nx / 2, ny = g.ny, pz = g.pz, px = g.px;
     dim3 gz(cdiv(g.nx / 2, c.fz.batch), g.ny, n);
-    LMVD_LAUNCH(c, KC_FFT_Z_INV, n * ny * h * fft_flops(pz), n * ny * h * 16.0 * ((g.nz - 1) + pz), k_fft_z_inv<C>,
-                gz, 256, smem_bytes(c.fz), c.fz, g, fi, T, tstride);
+    if (c.fz.ept == 12)
+      LMVD_LAUNCH(c, KC_FFT_Z_INV, n * ny * h * fft_flops(pz), n * ny * h * 16.0 * ((g.nz - 1) + pz),
+                  (k_fft_z_inv<C, 12>), gz, threads(c.fz), smem_bytes(c.fz), c.fz, g, fi, T, tstride);
+    else
+      LMVD_LAUNCH(c, KC_FFT_Z_INV, n * ny * h * fft_flops(pz), n * ny * h * 16.0 * ((g.nz - 1) + pz),
+                  (k_fft_z_inv<C, 6>), gz, threads(c.fz), smem_bytes(c.fz), c.fz, g, fi, T, tstride);
     dim3 gx(cdiv(cdiv(g.pz, 2), c.fx.batch), g.ny, n);
-    LMVD_LAUNCH(c, KC_FFT_X_INV, n * ny * ((g.pz + 1) / 2) * fft_flops(px), n * ny * pz * (16.0 * h + 8.0 * px),
-                k_fft_x_inv<C>, gx, 256, smem_bytes(c.fx), c.fx, g, T, tstride, fo);
+    if (c.fx.ept == 12)
+      LMVD_LAUNCH(c, KC_FFT_X_INV, n * ny * ((g.pz + 1) / 2) * fft_flops(px), n * ny * pz * (16.0 * h + 8.0 * px),
+                  (k_fft_x_inv<C, 12>), gx, threads(c.fx), smem_bytes(c.fx), c.fx, g, T, tstride, fo);
+    else
+      LMVD_LAUNCH(c, KC_FFT_X_INV, n * ny * ((g.pz + 1) / 2) * fft_flops(px), n * ny * pz * (16.0 * h + 8.0 * px),
+                  (k_fft_x_inv<C, 6>), gx, threads(c.fx), smem_bytes(c.fx), c.fx, g, T, tstride, fo);
   }
 }
 
@@ -406,11 +428,19 @@ static void forward_t(Ctx& c, void* const* in, cd* const* out, int nf) {
     }
     const double h = g.nx / 2, ny = g.ny, pz = g.pz, px = g.px;
     dim3 gx(cdiv(cdiv(g.pz, 2), c.fx.batch), g.ny, n);
-    LMVD_LAUNCH(c, KC_FFT_X_FWD, n * ny * ((g.pz + 1) / 2) * fft_flops(px), n * ny * pz * (16.0 * h + 8.0 * px),
-                k_fft_x_fwd<C>, gx, 256, smem_bytes(c.fx), c.fx, g, fi, T, tstride);
+    if (c.fx.ept == 12)
+      LMVD_LAUNCH(c, KC_FFT_X_FWD, n * ny * ((g.pz + 1) / 2) * fft_flops(px), n * ny * pz * (16.0 * h + 8.0 * px),
+                  (k_fft_x_fwd<C, 12>), gx, threads(c.fx), smem_bytes(c.fx), c.fx, g, fi, T, tstride);
+    else
+      LMVD_LAUNCH(c, KC_FFT_X_FWD, n * ny * ((g.pz + 1) / 2) * fft_flops(px), n * ny * pz * (16.0 * h + 8.0 * px),
+                  (k_fft_x_fwd<C, 6>), gx, threads(c.fx), smem_bytes(c.fx), c.fx, g, fi, T, tstride);
     dim3 gz(cdiv(g.nx / 2 + 1, c.fz.batch), g.ny, n);
-    LMVD_LAUNCH(c, KC_FFT_Z_FWD, n * ny * h * fft_flops(pz), n * ny * 16.0 * (pz * h + (double)g.nz * g.nxh),
-                k_fft_z_fwd<C>, gz, 256, smem_bytes(c.fz), c.fz, g, T, tstride, fo);
+    if (c.fz.ept == 12)
+      LMVD_LAUNCH(c, KC_FFT_Z_FWD, n * ny * h * fft_flops(pz), n * ny * 16.0 * (pz * h + (double)g.nz * g.nxh),
+                  (k_fft_z_fwd<C, 12>), gz, threads(c.fz), smem_bytes(c.fz), c.fz, g, T, tstride, fo);
+    else
+      LMVD_LAUNCH(c, KC_FFT_Z_FWD, n * ny * h * fft_flops(pz), n * ny * 16.0 * (pz * h + (double)g.nz * g.nxh),
+                  (k_fft_z_fwd<C, 6>), gz, threads(c.fz), smem_bytes(c.fz), c.fz, g, T, tstride, fo);
   }
 }
 
@@ -470,8 +500,10 @@ int noalloc_setup(int dev, void** ptr) {
   }
   void* p = nullptr;
   if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return LMVD_ERR_CUDA;
-  if (cudaFuncSetAttribute(k_fft_z_inv<cd>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess ||
-      cudaFuncSetAttribute(k_fft_x_inv<cd>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess)
+  if (cudaFuncSetAttribute(k_fft_z_inv<cd, 12>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess ||
+      cudaFuncSetAttribute(k_fft_x_inv<cd, 12>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess ||
+      cudaFuncSetAttribute(k_fft_z_inv<cd, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess ||
+      cudaFuncSetAttribute(k_fft_x_inv<cd, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess)
     return LMVD_ERR_CUDA;
   g_noalloc_ptr[dev] = p;
   *ptr = p;
@@ -500,11 +532,8 @@ extern "C" int lmvd_inverse_transform_noalloc(int nx, int ny, int nz, const void
   g.P = (size_t)g.px * g.pz;
   FFTPlan fx, fz;
   if (!make_plan(g.px, fx) || !make_plan(g.pz, fz)) return LMVD_ERR_UNSUPPORTED;
-  for (FFTPlan* p : {&fx, &fz}) {
-    int b = (int)(98304 / ((size_t)2 * (p->n + 1) * sizeof(cd)));
-    p->batch = b < 1 ? 1 : (b > 32 ? 32 : b);
+  for (FFTPlan* p : {&fx, &fz})
     if (smem_bytes(*p) > 200 * 1024) return LMVD_ERR_UNSUPPORTED;
-  }
   // scratch layout: x twiddles | z twiddles | one field's intermediate T[ny][pz][nx/2]
   const size_t off_tz = align256(sizeof(double2) * g.px);
   const size_t off_tb = off_tz + align256(sizeof(double2) * g.pz);
@@ -529,9 +558,11 @@ extern "C" int lmvd_inverse_transform_noalloc(int nx, int ny, int nz, const void
     fi.p[0] = (const cd*)spec + (size_t)f * S;
     fo.p[0] = phys + (size_t)f * P;
     dim3 gz(cdiv(nx / 2, fz.batch), ny, 1);
-    k_fft_z_inv<cd><<<gz, 256, smem_bytes(fz), st>>>(fz, g, fi, T, 0);
+    if (fz.ept == 12) k_fft_z_inv<cd, 12><<<gz, threads(fz), smem_bytes(fz), st>>>(fz, g, fi, T, 0);
+    else k_fft_z_inv<cd, 6><<<gz, threads(fz), smem_bytes(fz), st>>>(fz, g, fi, T, 0);
     dim3 gx(cdiv(cdiv(g.pz, 2), fx.batch), ny, 1);
-    k_fft_x_inv<cd><<<gx, 256, smem_bytes(fx), st>>>(fx, g, T, 0, fo);
+    if (fx.ept == 12) k_fft_x_inv<cd, 12><<<gx, threads(fx), smem_bytes(fx), st>>>(fx, g, T, 0, fo);
+    else k_fft_x_inv<cd, 6><<<gx, threads(fx), smem_bytes(fx), st>>>(fx, g, T, 0, fo);
   }
   return cudaGetLastError() == cudaSuccess ? LMVD_OK : LMVD_ERR_CUDA;
 }

@@ -82,6 +82,8 @@ struct FFTPlan {
   double2* tw = nullptr;   // tw[m] = (cos 2 pi m / n, sin 2 pi m / n), device
   float4* twf = nullptr;   // the same as double-float pairs (cos.hi, cos.lo, sin.hi, sin.lo), device
   int batch = 1;           // transforms per CTA
+  int ept = 12;            // elements per thread (a multiple of every radix of the plan)
+  int tpt = 1;             // threads per transform = n / ept; a CTA has tpt * batch threads
   double scale_d = 1.0;    // 1 / (px pz) for the forward z-pass
   df scale_f{1.f, 0.f};
   df s3f{0.f, 0.f};        // sin(2 pi / 3) as a double-float
