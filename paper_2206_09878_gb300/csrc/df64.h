@@ -3,9 +3,10 @@
 //
 // Built from error-free transformations: TwoSum (Knuth, TAOCP vol. 2, 4.2.2: s + e = a + b exactly
 // in 6 flops for any a, b), FastTwoSum (Dekker 1971: exact when |a| >= |b|) and the FMA form of
-// TwoProd (p + e = a * b exactly with e = fma(a, b, -p)). Sums renormalise with TwoSum so that
-// cancellation cannot break the |lo| <= ulp(hi)/2 invariant; products renormalise with FastTwoSum
-// (their correction term is always below ulp of the product).
+// TwoProd (p + e = a * b exactly with e = fma(a, b, -p)). The high parts are always added with
+// TwoSum; the final renormalisation uses FastTwoSum, whose result is exact except after a
+// cancellation of the high parts, where its error stays below ~2^-47 of the operands' magnitudes
+// (the normwise bound an FFT or a pointwise product needs).
 //
 // On GB300 an FP32 FMA issues 63x faster than an FP64 FMA, so transforms and pointwise products in
 // this arithmetic run several times faster than in FP64 while staying within ~1e-14 relative error.
@@ -29,23 +30,65 @@ __host__ __device__ inline double df_to_double(df a) { return (double)a.hi + (do
 
 // Split of a double into hi + lo with integer operations only (no FP64 instruction): hi takes the
 // sign, exponent and the top 23 stored mantissa bits (truncation), lo the remaining 29 bits rounded
-// to 24 by one int-to-float conversion and scaled by a power of two; a FastTwoSum renormalises.
-// Relative error <= 2^-48. Magnitudes outside [2^-66, 2^127) (and 0, inf, nan) take the FP64 route.
+// to 24 by one int-to-float conversion and scaled by two powers of two; a FastTwoSum renormalises.
+// Relative error <= 2^-48 for |x| >= 2^-102; smaller magnitudes keep hi exactly and lose lo gradually
+// (below 2^-126, outside the float range, the result is a signed zero). Magnitudes >= 2^128, inf and
+// nan take the FP64 conversion.
 __device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e);
 __device__ __forceinline__ df df_from_double_int(double x) {
   const unsigned long long u = (unsigned long long)__double_as_longlong(x);
   const unsigned hi32 = (unsigned)(u >> 32);
   const int e = (int)((hi32 >> 20) & 0x7ffu);
-  if (e < 957 || e > 1150) return df_from_double(x);
   const unsigned sign = hi32 & 0x80000000u;
+  if (e > 1150) return df_from_double(x);
+  if (e < 897) return df{__uint_as_float(sign), 0.f};
   const unsigned long long m52 = u & 0xFFFFFFFFFFFFFull;
   const float hi = __uint_as_float(sign | ((unsigned)(e - 896) << 23) | (unsigned)(m52 >> 29));
-  const float scale = __uint_as_float((unsigned)(e - 948) << 23);  // 2^(e - 1075)
-  float lo = __fmul_rn(__uint2float_rn((unsigned)(m52 & 0x1FFFFFFFull)), scale);
+  const int k = e - 1075;                                         // lo = rem * 2^k, k in [-178, 75]
+  const int ka = k >> 1, kb = k - ka;                             // 2^ka, 2^kb are normal floats
+  const float sa = __uint_as_float((unsigned)(ka + 127) << 23), sb = __uint_as_float((unsigned)(kb + 127) << 23);
+  float lo = __fmul_rn(__fmul_rn(__uint2float_rn((unsigned)(m52 & 0x1FFFFFFFull)), sa), sb);
   lo = sign ? -lo : lo;
   float s, l;
   fast_two_sum(hi, lo, s, l);
   return df{s, l};
+}
+
+// hi + lo rounded to a double with integer operations only (no FP64 instruction). The 24-bit
+// mantissa of lo is aligned to the 53-bit mantissa of hi and added (or subtracted); bits of lo below
+// the double's last place are rounded to nearest (a denormal lo is handled like a normal one).
+// Non-normal hi (denormal, inf, nan) takes the FP64 route.
+__device__ __forceinline__ double df_to_double_int(df a) {
+  const unsigned hb = __float_as_uint(a.hi), lb = __float_as_uint(a.lo);
+  const unsigned long long sgn = (unsigned long long)(hb & 0x80000000u) << 32;
+  if ((hb & 0x7fffffffu) == 0) return __longlong_as_double((long long)sgn);  // a normalised pair has lo = 0 here
+  int eh = (int)((hb >> 23) & 0xffu);
+  if (eh == 0 || eh == 255) return (double)a.hi + (double)a.lo;
+  unsigned long long M = (unsigned long long)((hb & 0x7fffffu) | 0x800000u) << 29;  // leading bit 52
+  int el = (int)((lb >> 23) & 0xffu);
+  if ((lb & 0x7fffffffu) != 0 && el != 255) {
+    // a denormal lo has no implicit bit and the exponent of the smallest normal
+    const unsigned long long ml = (unsigned long long)((lb & 0x7fffffu) | (el ? 0x800000u : 0u));
+    el = el ? el : 1;
+    const int sh = 29 - (eh - el);
+    unsigned long long add = 0;
+    if (sh >= 0) add = ml << sh;
+    else if (sh > -26) add = (ml + (1ull << (-sh - 1))) >> (-sh);
+    if (((hb ^ lb) & 0x80000000u) == 0) {
+      M += add;
+      if (M >> 53) {
+        M = (M + 1) >> 1;
+        ++eh;
+      }
+    } else {
+      M -= add;
+      if (!(M >> 52)) {
+        M <<= 1;
+        --eh;
+      }
+    }
+  }
+  return __longlong_as_double((long long)(sgn | ((unsigned long long)(eh + 896) << 52) | (M & 0xFFFFFFFFFFFFFull)));
 }
 
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
@@ -62,7 +105,7 @@ __device__ __forceinline__ df dadd(df a, df b) {
   float s, e, r, rl;
   two_sum(a.hi, b.hi, s, e);
   e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
-  two_sum(s, e, r, rl);
+  fast_two_sum(s, e, r, rl);
   return df{r, rl};
 }
 __device__ __forceinline__ df dneg(df a) { return df{-a.hi, -a.lo}; }
@@ -90,7 +133,7 @@ __device__ __forceinline__ df ddot2(df a, df b, df c, df d) {
   t = __fmaf_rn(c.hi, d.lo, t);
   t = __fmaf_rn(c.lo, d.hi, t);
   float r, rl;
-  two_sum(s, t, r, rl);
+  fast_two_sum(s, t, r, rl);
   return df{r, rl};
 }
 // 1 / a: float estimate refined by one Newton step in df arithmetic (relative error ~2^-46)

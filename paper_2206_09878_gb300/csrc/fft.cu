@@ -94,7 +94,7 @@ struct FT<cdf> {
   }
   __device__ static cdf from_spec(cd x) { return cdf{df_from_double_int(x.re), df_from_double_int(x.im)}; }
   __device__ static cd to_spec(cdf x, const FFTPlan& p) {
-    return cd{df_to_double(dmul(x.re, p.scale_f)), df_to_double(dmul(x.im, p.scale_f))};
+    return cd{df_to_double_int(dmul(x.re, p.scale_f)), df_to_double_int(dmul(x.im, p.scale_f))};
   }
   __device__ static cdf make(R a, R b) { return cdf{a, b}; }
   __device__ static R re(cdf a) { return a.re; }
@@ -158,12 +158,19 @@ __device__ __forceinline__ void fft_stage(C* x, const FFTPlan& pl, int L, int tt
 template <class C, int SIGN, int EPT>
 __device__ void fft_inplace(C* x, const FFTPlan& pl, int tt, int tpt) {
   int L = 1;
-  for (int s = 0; s < pl.nst; ++s) {
-    const int r = pl.radix[s];
-    if (r == 4) fft_stage<C, SIGN, 4, EPT>(x, pl, L, tt, tpt);
-    else if (r == 3) fft_stage<C, SIGN, 3, EPT>(x, pl, L, tt, tpt);
-    else fft_stage<C, SIGN, 2, EPT>(x, pl, L, tt, tpt);
-    L *= r;
+  unsigned code = pl.code;
+  for (int s = 0; s < pl.nst; ++s, code >>= 2) {
+    const unsigned r2 = code & 3u;
+    if (r2 == 0) {
+      fft_stage<C, SIGN, 4, EPT>(x, pl, L, tt, tpt);
+      L *= 4;
+    } else if (r2 == 2) {
+      fft_stage<C, SIGN, 3, EPT>(x, pl, L, tt, tpt);
+      L *= 3;
+    } else {
+      fft_stage<C, SIGN, 2, EPT>(x, pl, L, tt, tpt);
+      L *= 2;
+    }
   }
 }
 
@@ -312,7 +319,10 @@ static bool make_plan(int n, FFTPlan& p) {
   while (m % 4 == 0) { p.radix[p.nst++] = 4; m /= 4; }
   while (m % 2 == 0) { p.radix[p.nst++] = 2; m /= 2; }
   while (m % 3 == 0) { p.radix[p.nst++] = 3; m /= 3; }
-  if (m != 1 || p.nst >= 24) return false;
+  if (m != 1 || p.nst > 16) return false;
+  p.code = 0;
+  for (int s2 = 0; s2 < p.nst; ++s2)
+    p.code |= (unsigned)(p.radix[s2] == 4 ? 0 : (p.radix[s2] == 2 ? 1 : 2)) << (2 * s2);
   p.ept = (n % 12 == 0) ? 12 : ((n % 6 == 0) ? 6 : 0);
   if (!p.ept) return false;
   p.tpt = n / p.ept;

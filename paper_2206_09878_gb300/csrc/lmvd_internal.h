@@ -79,6 +79,7 @@ struct FFTPlan {
   int n = 0;
   int nst = 0;
   int radix[24];
+  unsigned code = 0;       // the radix sequence, 2 bits per stage (0: 4, 1: 2, 2: 3), first stage lowest
   double2* tw = nullptr;   // tw[m] = (cos 2 pi m / n, sin 2 pi m / n), device
   float4* twf = nullptr;   // the same as double-float pairs (cos.hi, cos.lo, sin.hi, sin.lo), device
   int batch = 1;           // transforms per CTA
