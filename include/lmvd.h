@@ -167,6 +167,24 @@ int lmvd_forward_transform(lmvd_ctx* ctx, const double* phys, void* spec, int nf
 int lmvd_inverse_transform_noalloc(int nx, int ny, int nz, const void* spec, double* phys, int nfields,
                                    void* cuda_stream);
 
+/* Adjoint of one substage (the differentiation path; the paper's method is differentiated, the paper
+ * itself has no adjoint). Let x = (state, history) be the context's current state and history and
+ * y = (state', history') what lmvd_advance_substage would produce from it. Given ybar, this computes
+ * xbar = J(x)^T ybar, with the inner products sum Re(conj(a) b) over every stored complex entry and
+ * sum a b over the real arrays. Every linear step is transposed exactly (transposed banded evaluations
+ * and band solves, transforms G^T = (px pz) W F and F^T = G W^{-1} / (px pz) with W = 1 at kx = 0 and 2
+ * at kx > 0); the products of Sec. 2.1, 4.3 and Eq. om / phi are differentiated at the fields of a
+ * forward substage that this call runs first, so the context advances by one substage as a side effect.
+ * state blobs (lmvd_state_bytes): z_hat | omega2_hat | m2d_hat | mean_m1 | mean_m3, packed in this order
+ * in the layouts of lmvd_set_state; history blobs: as lmvd_get_state (the leading counter is ignored on
+ * input and set to the substage index on output). Pointers: host or device memory, caller-owned.
+ * Synchronous. Allocates the adjoint workspace on its first call (tape of the physical fields plus the
+ * adjoint fields, about 45 spectral and 44 physical fields).
+ * Errors: INVALID_ARG (NULL), UNSUPPORTED (precision 1 or kf > 15), OOM, CUDA. */
+size_t lmvd_state_bytes(const lmvd_ctx* ctx);
+int lmvd_adjoint_substage(lmvd_ctx* ctx, const void* state_bar_out, const void* history_bar_out,
+                          void* state_bar_in, void* history_bar_in);
+
 /* Substage counter s (0 after a start-up). -1 if ctx is NULL. */
 int lmvd_substage_index(const lmvd_ctx* ctx);
 

@@ -10,7 +10,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblmvd.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["api.cu", "fft.cu", "ykernels.cu", "pointwise.cu", "basis.cpp"]
+SOURCES = ["api.cu", "fft.cu", "ykernels.cu", "pointwise.cu", "adjoint.cu", "basis.cpp"]
 
 
 def _nvcc():

@@ -279,8 +279,13 @@ void solve_interp(Ctx& c, std::initializer_list<SolveJob> jobs, const DLU& lu) {
               dim3(mode_blocks(c.g), n), TPB_MODE, 0, c.g, lu, sj);
 }
 
-// steps 1-2: m^d and z-derived fields in physical space; rho, 1/rho, f', grad z / rho; R_z
-void physical_pass_1(Ctx& c) {
+// steps 1-2: m^d and z-derived fields in physical space; rho, 1/rho, f', grad z / rho; R_z.
+// zp: where z, dz/dx, dz/dz, dz/dy, lap z land on the physical grid (work fields by default; the adjoint
+// keeps them).
+void physical_pass_1(Ctx& c, double* const* zp = nullptr) {
+  double* zf[5] = {c.pw[0], c.pw[1], c.pw[2], c.pw[3], c.pw[4]};
+  if (zp)
+    for (int f = 0; f < 5; ++f) zf[f] = zp[f];
   Fields8 o{};
   for (int f = 0; f < 8; ++f) o.p[f] = c.sv[f];
   const double SM = (double)c.g.ny * c.g.M;
@@ -288,17 +293,17 @@ void physical_pass_1(Ctx& c) {
               mode_blocks(c.g), TPB_MODE, 0, c.g, c.B0g, c.B1g, c.B2g, c.Sg0, c.Sg1, c.z, c.om, c.m2, c.mm1, c.mm3, o);
   // physical: z, zx, zz, zy, lapz -> pw[0..4]; m^d -> md[0..2]
   cd* in[8] = {c.sv[0], c.sv[1], c.sv[2], c.sv[3], c.sv[4], c.sv[5], c.sv[6], c.sv[7]};
-  double* out[8] = {c.pw[0], c.pw[1], c.pw[2], c.pw[3], c.pw[4], c.md[0], c.md[1], c.md[2]};
+  double* out[8] = {zf[0], zf[1], zf[2], zf[3], zf[4], c.md[0], c.md[1], c.md[2]};
   fft_inverse(c, in, out, 8);
   const size_t n = (size_t)c.g.ny * c.g.P;
   EosArgs e{c.cfg.rho_heavy, c.cfg.rho_light, 1.0 / (c.cfg.re * c.cfg.sc)};
   if (c.cfg.precision == 1)
-    LMVD_LAUNCH(c, KC_PRODUCTS, 25.0 * n, 8.0 * 15 * n, k_products_p1_df, elem_blocks(n), 256, 0, n, e, c.pw[0],
-                c.pw[1], c.pw[2], c.pw[3], c.pw[4], c.md[0], c.md[1], c.md[2], c.rho, c.invrho, c.fprime, c.w[0],
+    LMVD_LAUNCH(c, KC_PRODUCTS, 25.0 * n, 8.0 * 15 * n, k_products_p1_df, elem_blocks(n), 256, 0, n, e, zf[0],
+                zf[1], zf[2], zf[3], zf[4], c.md[0], c.md[1], c.md[2], c.rho, c.invrho, c.fprime, c.w[0],
                 c.w[1], c.w[2], c.pw[5]);
   else
-    LMVD_LAUNCH(c, KC_PRODUCTS, 25.0 * n, 8.0 * 15 * n, k_products_p1, elem_blocks(n), 256, 0, n, e, c.pw[0],
-                c.pw[1], c.pw[2], c.pw[3], c.pw[4], c.md[0], c.md[1], c.md[2], c.rho, c.invrho, c.fprime, c.w[0],
+    LMVD_LAUNCH(c, KC_PRODUCTS, 25.0 * n, 8.0 * 15 * n, k_products_p1, elem_blocks(n), 256, 0, n, e, zf[0],
+                zf[1], zf[2], zf[3], zf[4], c.md[0], c.md[1], c.md[2], c.rho, c.invrho, c.fprime, c.w[0],
                 c.w[1], c.w[2], c.pw[5]);
   double* fin[1] = {c.pw[5]};
   cd* fout[1] = {c.sv[0]};
@@ -306,20 +311,25 @@ void physical_pass_1(Ctx& c) {
   solve_interp(c, {SolveJob{c.sv[0], nullptr, c.Rz}}, c.lu_interp);
 }
 
-// rho_t = P[f'(z) zdot] and m^c = C(rho_t) (B coefficients), then m^c on the physical grid in pw[0..2]
-void mc_from_zdot(Ctx& c) {
+// rho_t = P[f'(z) zdot] and m^c = C(rho_t) (B coefficients), then m^c on the physical grid.
+// a: where zdot lands on the physical grid; b: where m^c lands (work fields by default).
+void mc_from_zdot(Ctx& c, double* a = nullptr, double* const* b = nullptr) {
   const size_t n = (size_t)c.g.ny * c.g.P;
-  eval_jobs(c, {EvalJob{c.B0g, c.zdot, c.sv[0]}});
+  if (!a) a = c.pw[0];
+  double* bb[3] = {c.pw[0], c.pw[1], c.pw[2]};
+  if (b)
+    for (int f = 0; f < 3; ++f) bb[f] = b[f];
+  eval_jobs(c, {EvalJob{c.B0g, c.zdot, c.sv[0], 0}});
   {
     cd* in[1] = {c.sv[0]};
-    double* out[1] = {c.pw[0]};
+    double* out[1] = {a};
     fft_inverse(c, in, out, 1);
   }
   if (c.cfg.precision == 1)
-    LMVD_LAUNCH(c, KC_PRODUCTS, 1.0 * n, 24.0 * n, k_product_rt_df, elem_blocks(n), 256, 0, n, c.fprime, c.pw[0],
+    LMVD_LAUNCH(c, KC_PRODUCTS, 1.0 * n, 24.0 * n, k_product_rt_df, elem_blocks(n), 256, 0, n, c.fprime, a,
                 c.pw[1]);
   else
-    LMVD_LAUNCH(c, KC_PRODUCTS, 1.0 * n, 24.0 * n, k_product_rt, elem_blocks(n), 256, 0, n, c.fprime, c.pw[0], c.pw[1]);
+    LMVD_LAUNCH(c, KC_PRODUCTS, 1.0 * n, 24.0 * n, k_product_rt, elem_blocks(n), 256, 0, n, c.fprime, a, c.pw[1]);
   {
     double* in[1] = {c.pw[1]};
     cd* out[1] = {c.sv[1]};
@@ -332,22 +342,24 @@ void mc_from_zdot(Ctx& c) {
                 rowsM * (16.0 * 4 + 8.0 * (2 * c.lu_mc.K + 1)), k_mc_solve, mode_blocks(c.g), TPB_MODE, 0, c.g,
                 c.lu_mc, c.Bs[1], c.dstar, c.rt, c.m1c, c.m2c, c.m3c);
   }
-  eval_jobs(c, {EvalJob{c.B0g, c.m1c, c.sv[0]}, EvalJob{c.Sg0, c.m2c, c.sv[1]}, EvalJob{c.B0g, c.m3c, c.sv[2]}});
+  eval_jobs(c, {EvalJob{c.B0g, c.m1c, c.sv[0], 0}, EvalJob{c.Sg0, c.m2c, c.sv[1], 0}, EvalJob{c.B0g, c.m3c, c.sv[2], 0}});
   cd* in[3] = {c.sv[0], c.sv[1], c.sv[2]};
-  double* out[3] = {c.pw[0], c.pw[1], c.pw[2]};
-  fft_inverse(c, in, out, 3);
+  fft_inverse(c, in, bb, 3);
 }
 
 // one application of the fixed point (Eq. y_k): zdot <- L(z) zdot + R_z
-void fp_apply(Ctx& c) {
-  mc_from_zdot(c);
+void fp_apply(Ctx& c, double* a = nullptr, double* const* b = nullptr) {
+  mc_from_zdot(c, a, b);
+  double* bb[3] = {c.pw[0], c.pw[1], c.pw[2]};
+  if (b)
+    for (int f = 0; f < 3; ++f) bb[f] = b[f];
   const size_t n = (size_t)c.g.ny * c.g.P;
   if (c.cfg.precision == 1)
     LMVD_LAUNCH(c, KC_PRODUCTS, 6.0 * n, 56.0 * n, k_product_L_df, elem_blocks(n), 256, 0, n, c.w[0], c.w[1], c.w[2],
-                c.pw[0], c.pw[1], c.pw[2], c.pw[3]);
+                bb[0], bb[1], bb[2], c.pw[3]);
   else
     LMVD_LAUNCH(c, KC_PRODUCTS, 6.0 * n, 56.0 * n, k_product_L, elem_blocks(n), 256, 0, n, c.w[0], c.w[1], c.w[2],
-                c.pw[0], c.pw[1], c.pw[2], c.pw[3]);
+                bb[0], bb[1], bb[2], c.pw[3]);
   double* in[1] = {c.pw[3]};
   cd* out[1] = {c.sv[3]};
   fft_forward(c, in, out, 1);
@@ -369,14 +381,14 @@ void startup(Ctx& c) {
   c.s = 0;
 }
 
-int advance(Ctx& c) {
+int advance_impl(Ctx& c, const Tape* tape) {
   const Grid& g = c.g;
   const lmvd_config& cf = c.cfg;
   const size_t S = (size_t)g.ny * g.M;
   const size_t n = (size_t)g.ny * g.P;
   const bool stage_n = (c.s % 2) == 0;
   // steps 1-2
-  physical_pass_1(c);
+  physical_pass_1(c, tape ? tape->zp : nullptr);
   double a[4];
   if (stage_n) {
     const double b = cf.beta_n;
@@ -388,17 +400,20 @@ int advance(Ctx& c) {
   LMVD_LAUNCH(c, KC_MISC, 16.0 * S, 80.0 * S, k_bdf, elem_blocks(S), 256, 0, S, a[0], a[1], a[2], a[3], 1.0 / cf.dt,
               c.z, c.zh[0], c.zh[1], c.zh[2], c.zdot);
   // step 3
-  for (int k = 0; k < cf.kf; ++k) fp_apply(c);
-  mc_from_zdot(c);
+  for (int k = 0; k < cf.kf; ++k) fp_apply(c, tape ? tape->a[k] : nullptr, tape ? tape->b[k] : nullptr);
+  mc_from_zdot(c, tape ? tape->a[cf.kf] : nullptr, tape ? tape->b[cf.kf] : nullptr);
+  const double* mcp[3] = {c.pw[0], c.pw[1], c.pw[2]};
+  if (tape)
+    for (int f = 0; f < 3; ++f) mcp[f] = tape->b[cf.kf][f];
   // steps 4-5: products with m = m^d + m^c, forward transforms, RHS streams, collocation solves, RHS
   P2Out q{};
   for (int f = 0; f < 10; ++f) q.p[f] = c.pw[f];
   if (cf.precision == 1)
     LMVD_LAUNCH(c, KC_PRODUCTS, 18.0 * n, 8.0 * 18 * n, k_products_p2_df, elem_blocks(n), 256, 0, n, c.md[0],
-                c.md[1], c.md[2], c.pw[0], c.pw[1], c.pw[2], c.rho, c.invrho, q);
+                c.md[1], c.md[2], mcp[0], mcp[1], mcp[2], c.rho, c.invrho, q);
   else
     LMVD_LAUNCH(c, KC_PRODUCTS, 18.0 * n, 8.0 * 18 * n, k_products_p2, elem_blocks(n), 256, 0, n, c.md[0], c.md[1],
-                c.md[2], c.pw[0], c.pw[1], c.pw[2], c.rho, c.invrho, q);
+                c.md[2], mcp[0], mcp[1], mcp[2], c.rho, c.invrho, q);
   fft_forward(c, c.pw, c.sv, 10);
   Fields10C svc{};
   for (int f = 0; f < 10; ++f) svc.p[f] = c.sv[f];
@@ -453,6 +468,14 @@ int advance(Ctx& c) {
   c.s += 1;
   return cuda_check(c);
 }
+
+}  // namespace
+
+namespace lmvd {
+int advance(Ctx& c, const Tape* tape) { return advance_impl(c, tape); }
+}  // namespace lmvd
+
+namespace {
 
 bool valid_cfg(const lmvd_config& f) {
   if (f.nx < 4 || f.nz < 4 || (f.nx % 2) || (f.nz % 2)) return false;
@@ -586,6 +609,7 @@ void lmvd_destroy(lmvd_ctx* h) {
   Ctx& c = h->c;
   if (c.stream) cudaStreamSynchronize(c.stream);
   else cudaDeviceSynchronize();
+  adj_destroy(c);
   for (auto& p : c.prof.pending) {
     cudaEventDestroy(p.a);
     cudaEventDestroy(p.b);
@@ -663,13 +687,13 @@ int lmvd_get_state(lmvd_ctx* h, void* z, void* om, void* m2, double* mm1, double
 
 int lmvd_advance_substage(lmvd_ctx* h) {
   if (!h) return LMVD_ERR_INVALID_ARG;
-  return advance(h->c);
+  return advance_impl(h->c, nullptr);
 }
 
 int lmvd_step(lmvd_ctx* h, int nsteps) {
   if (!h || nsteps < 0) return LMVD_ERR_INVALID_ARG;
   for (int i = 0; i < 2 * nsteps; ++i) {
-    int e = advance(h->c);
+    int e = advance_impl(h->c, nullptr);
     if (e) return e;
   }
   return LMVD_OK;
@@ -744,6 +768,18 @@ int lmvd_forward_transform(lmvd_ctx* h, const double* phys, void* spec, int nfie
     fft_forward_as(c, in, out, n, 0);
   }
   return cuda_check(c);
+}
+
+size_t lmvd_state_bytes(const lmvd_ctx* h) {
+  if (!h) return 0;
+  const Grid& g = h->c.g;
+  return sizeof(cd) * g.M * ((size_t)3 * g.ny + 1) + sizeof(double) * 2 * g.ny;
+}
+
+int lmvd_adjoint_substage(lmvd_ctx* h, const void* sbar_out, const void* hbar_out, void* sbar_in, void* hbar_in) {
+  if (!h || !sbar_out || !hbar_out || !sbar_in || !hbar_in) return LMVD_ERR_INVALID_ARG;
+  const int e = adjoint_substage(h->c, sbar_out, hbar_out, sbar_in, hbar_in);
+  return e ? latch(h->c, e) : LMVD_OK;
 }
 
 int lmvd_substage_index(const lmvd_ctx* h) { return h ? h->c.s : -1; }

@@ -131,6 +131,51 @@ DiagBand to_diag(const RowBand& m, int K) {
   return d;
 }
 
+RowBand transpose(const RowBand& m) {
+  RowBand t;
+  t.rows = m.cols;
+  t.cols = m.rows;
+  std::vector<int> lo(t.rows, t.cols), hi(t.rows, -1);
+  for (int i = 0; i < m.rows; ++i)
+    for (int q = 0; q < m.w; ++q) {
+      const int j = m.c0[i] + q;
+      if (j < 0 || j >= m.cols || m.v[(size_t)i * m.w + q] == 0.0) continue;
+      lo[j] = std::min(lo[j], i);
+      hi[j] = std::max(hi[j], i);
+    }
+  t.w = 1;
+  for (int j = 0; j < t.rows; ++j)
+    if (hi[j] >= lo[j]) t.w = std::max(t.w, hi[j] - lo[j] + 1);
+  t.w = std::min(t.w, t.cols);
+  t.c0.assign(t.rows, 0);
+  t.v.assign((size_t)t.rows * t.w, 0.0);
+  for (int j = 0; j < t.rows; ++j) {
+    int c = hi[j] >= lo[j] ? lo[j] : 0;
+    t.c0[j] = std::max(0, std::min(c, t.cols - t.w));
+  }
+  for (int i = 0; i < m.rows; ++i)
+    for (int q = 0; q < m.w; ++q) {
+      const int j = m.c0[i] + q;
+      const double v = m.v[(size_t)i * m.w + q];
+      if (j < 0 || j >= m.cols || v == 0.0) continue;
+      t.v[(size_t)j * t.w + (i - t.c0[j])] = v;
+    }
+  return t;
+}
+
+DiagBand transpose(const DiagBand& a) {
+  DiagBand t;
+  t.n = a.n;
+  t.K = a.K;
+  t.a.assign(a.a.size(), 0.0);
+  for (int i = 0; i < a.n; ++i)
+    for (int q = -a.K; q <= a.K; ++q) {
+      const int j = i + q;
+      if (j >= 0 && j < a.n) t.el(j, i) = a.get(i, j);
+    }
+  return t;
+}
+
 void band_profile(const DiagBand& A2, const DiagBand& A0, std::vector<int>& nl, std::vector<int>& nu) {
   const int n = A2.n, K = A2.K;
   nl.assign(n, 0);

@@ -44,6 +44,9 @@ std::vector<double> greville(const Knots& k);
 int eval_nonzero(const Knots& k, double x, int deriv, double* vals);
 RowBand collocation(const Knots& k, const std::vector<double>& pts, int deriv);
 DiagBand to_diag(const RowBand& m, int K);
+// Transposes (used by the adjoint): the transpose of a banded matrix is banded.
+RowBand transpose(const RowBand& m);
+DiagBand transpose(const DiagBand& a);
 
 // No-pivoting LU of a band matrix (stable here: the y-systems have growth factor ~1).
 // L multipliers lo[i*K + q-1] (q = 1..K, multiplier of row i-q); U: up[i*K + r-1] (r = 1..K),

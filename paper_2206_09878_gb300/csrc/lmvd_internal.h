@@ -108,6 +108,16 @@ struct Prof {
   std::vector<cudaEvent_t> pool;
 };
 
+// ---------------------------------------------------------------- adjoint support
+constexpr int KF_MAX_ADJ = 15;
+// Physical fields of one forward substage that the adjoint of the products needs.
+struct Tape {
+  double* zp[5];                   // z, dz/dx, dz/dz, dz/dy, lap z (pass 1)
+  double* a[KF_MAX_ADJ + 1];       // dz/dt^{k-1} on the grid, k = 1 .. kf + 1 (the last for the final m^c)
+  double* b[KF_MAX_ADJ + 1][3];    // m^c(dz/dt^{k-1}) on the grid
+};
+struct AdjWork;
+
 // ---------------------------------------------------------------- context
 struct Ctx {
   lmvd_config cfg;
@@ -148,7 +158,14 @@ struct Ctx {
   double* pw[10];     // physical work fields
 
   Prof prof;
+  AdjWork* adj = nullptr;
 };
+
+// one substage (api.cu); with a tape the physical fields the adjoint needs are kept
+int advance(Ctx& c, const Tape* tape);
+// adjoint of one substage (adjoint.cu); blobs as documented for lmvd_adjoint_substage
+int adjoint_substage(Ctx& c, const void* sbar_out, const void* hbar_out, void* sbar_in, void* hbar_in);
+void adj_destroy(Ctx& c);
 
 // Bracket a launch: counts it, and with profiling on records CUDA events around it on the stream.
 cudaEvent_t prof_begin(Ctx& c);

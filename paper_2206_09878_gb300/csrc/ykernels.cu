@@ -4,63 +4,10 @@
 // Paper: Sec. 4.1 (m^d, Eq. phi_poisson, md_recon), Sec. 4.2 (m^c, Eq. COM_fourier, CF_fourier,
 // mc_recon, mc_mean), Sec. 4.4 (Eq. DNS_system, Algorithm 2), Sec. 3.2-3.3 (Eq. dzdt_guesses,
 // midpoint RK2), Appendix C (B-spline spaces and the exact derivative map D*).
+#include "band.cuh"
 #include "ykernels.h"
 
 namespace lmvd {
-
-// ------------------------------------------------------------------ band LU access
-__device__ inline double lu_lo(const DLU& f, int i, int q, int m) {
-  return __ldg(f.lo + (f.mstride ? ((size_t)(i * f.K + q - 1) * f.mstride + m) : (size_t)(i * f.K + q - 1)));
-}
-__device__ inline double lu_up(const DLU& f, int i, int r, int m) {
-  return __ldg(f.up + (f.mstride ? ((size_t)(i * f.K + r - 1) * f.mstride + m) : (size_t)(i * f.K + r - 1)));
-}
-__device__ inline double lu_invd(const DLU& f, int i, int m) {
-  return __ldg(f.invd + (f.mstride ? ((size_t)i * f.mstride + m) : (size_t)i));
-}
-
-// Forward then backward substitution of L U x = rhs for mode m.
-// rhs(i) gives row i of the right-hand side; y is scratch of n rows (stride M) that may alias the
-// output; out(i, x_i, x_{i+1}) receives the solution in decreasing i.
-template <class Rhs, class Out>
-__device__ void band_solve(const DLU& f, int m, cd* y, size_t M, Rhs rhs, Out out) {
-  cd win[KMAX];
-#pragma unroll
-  for (int q = 0; q < KMAX; ++q) win[q] = mk(0, 0);
-  for (int i = 0; i < f.n; ++i) {
-    cd v = rhs(i);
-    const int nl = __ldg(f.nl + i);
-#pragma unroll
-    for (int q = 1; q <= KMAX; ++q)
-      if (q <= nl) v = fma_rc(-lu_lo(f, i, q, m), win[q - 1], v);
-#pragma unroll
-    for (int q = KMAX - 1; q > 0; --q) win[q] = win[q - 1];
-    win[0] = v;
-    y[(size_t)i * M + m] = v;
-  }
-#pragma unroll
-  for (int q = 0; q < KMAX; ++q) win[q] = mk(0, 0);
-  for (int i = f.n - 1; i >= 0; --i) {
-    cd v = y[(size_t)i * M + m];
-    const int nu = __ldg(f.nu + i);
-#pragma unroll
-    for (int r = 1; r <= KMAX; ++r)
-      if (r <= nu) v = fma_rc(-lu_up(f, i, r, m), win[r - 1], v);
-    v = lu_invd(f, i, m) * v;
-    out(i, v, win[0]);
-#pragma unroll
-    for (int q = KMAX - 1; q > 0; --q) win[q] = win[q - 1];
-    win[0] = v;
-  }
-}
-
-__device__ inline double band_row_real(const DBand& B, int i, const double* x) {
-  const int c = B.c0[i];
-  const double* v = B.v + (size_t)i * B.w;
-  double acc = 0.0;
-  for (int q = 0; q < B.w; ++q) acc = fma(__ldg(v + q), x[c + q], acc);
-  return acc;
-}
 
 // ------------------------------------------------------------------ step 1-2 inputs: values at g
 // out[0..7] = z, dz/dx, dz/dz, dz/dy, lap z, m1^d, m2^d, m3^d at the Greville points of the order-p space.
@@ -105,13 +52,18 @@ __global__ void k_eval_p1(Grid g, DBand B0g, DBand B1g, DBand B2g, DBand Sg0, DB
 }
 
 // ------------------------------------------------------------------ generic values at points
-// job blockIdx.y: out = B in (rows B.rows), Nyquist modes zero.
+// job blockIdx.y: out = B in (or out += B in), rows B.rows; Nyquist modes zero (or unchanged).
 __global__ void k_eval(Grid g, EvalJobs jobs) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= (int)g.M) return;
   const EvalJob& jb = jobs.j[blockIdx.y];
   const size_t M = g.M;
   const bool ny = is_nyquist(g, m);
+  if (jb.acc) {
+    if (ny) return;
+    for (int i = 0; i < jb.B.rows; ++i) jb.out[(size_t)i * M + m] = jb.out[(size_t)i * M + m] + band_row(jb.B, i, jb.in, M, m);
+    return;
+  }
   for (int i = 0; i < jb.B.rows; ++i)
     jb.out[(size_t)i * M + m] = ny ? mk(0, 0) : band_row(jb.B, i, jb.in, M, m);
 }

@@ -20,6 +20,7 @@ struct EvalJob {
   DBand B;
   const cd* in;
   cd* out;
+  int acc;  // 1: out += B in
 };
 struct EvalJobs {
   EvalJob j[4];

@@ -66,6 +66,8 @@ def _load():
         "lmvd_inverse_transform": (I, [P, P, P, I]),
         "lmvd_forward_transform": (I, [P, P, P, I]),
         "lmvd_inverse_transform_noalloc": (I, [I, I, I, P, P, I, P]),
+        "lmvd_state_bytes": (S, [P]),
+        "lmvd_adjoint_substage": (I, [P, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -81,7 +83,8 @@ EXPORTED = ("lmvd_default_config", "lmvd_create", "lmvd_destroy", "lmvd_set_stat
             "lmvd_history_bytes", "lmvd_advance_substage", "lmvd_step", "lmvd_get_field", "lmvd_field_bytes",
             "lmvd_substage_index", "lmvd_synchronize", "lmvd_status", "lmvd_strerror", "lmvd_profile_enable",
             "lmvd_profile_read", "lmvd_kernel_class_name", "lmvd_kernel_launches", "lmvd_inverse_transform",
-            "lmvd_forward_transform", "lmvd_inverse_transform_noalloc")
+            "lmvd_forward_transform", "lmvd_inverse_transform_noalloc", "lmvd_state_bytes",
+            "lmvd_adjoint_substage")
 LMVD_KERNEL_CLASSES = 13
 
 
@@ -202,6 +205,15 @@ def lmvd_inverse_transform_noalloc(nx, ny, nz, spec, phys, nfields, stream=None)
     _check(_lib.lmvd_inverse_transform_noalloc(int(nx), int(ny), int(nz), _ptr(spec), _ptr(phys), int(nfields),
                                                ctypes.c_void_p(stream.cuda_stream)),
            "lmvd_inverse_transform_noalloc")
+
+
+def lmvd_state_bytes(h):
+    return int(_lib.lmvd_state_bytes(h))
+
+
+def lmvd_adjoint_substage(h, state_bar_out, history_bar_out, state_bar_in, history_bar_in):
+    _check(_lib.lmvd_adjoint_substage(h, _ptr(state_bar_out), _ptr(history_bar_out), _ptr(state_bar_in),
+                                      _ptr(history_bar_in)), "lmvd_adjoint_substage")
 
 
 # ---------------------------------------------------------------- convenience (still marshalling only)
