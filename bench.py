@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", type=int, default=0, help="0: FP64; 1: double-float transforms/products")
     ap.add_argument("--no-variant", action="store_true", help="skip timing the other precision")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/forward cost ratio")
+    ap.add_argument("--adjoint-workload", default="rt128")
     return ap.parse_args()
 
 
@@ -279,6 +281,53 @@ def roofline_of(prof, ms_step_total, fp):
             "share_of_step": tms / ms_step_total if ms_step_total > 0 else None}
 
 
+def adjoint_ratio(L, name, stream, reps=3):
+    """Cost of lmvd_adjoint_substage (which re-runs the forward substage with a tape) against one forward
+    substage, FP64, on the given workload; CUDA events on the library stream, after one warm-up each."""
+    import numpy as np
+    import torch
+
+    from paper_2206_09878_gb300.rt_inputs import rt_state
+    w, _ = workload_config(name)
+    cfg = L.lmvd_default_config(w["nx"], w["ny"], w["nz"], re=w["re"], rho_light=1.0 / w["ratio"], dt=w["dt"],
+                                n_startup=4)
+    ctx = L.Context(cfg, stream=stream)
+    ctx.set_state({k: torch.from_numpy(np.ascontiguousarray(v)).cuda() for k, v in rt_state(**w).items()})
+    ctx.advance_substage()
+    hist = ctx.history_buffer()
+    st = ctx.get_state(history=hist)
+    sb = torch.zeros(L.lmvd_state_bytes(ctx.h), dtype=torch.uint8, device="cuda")
+    hb_in = torch.zeros_like(hist)
+    ybar_s = torch.ones(L.lmvd_state_bytes(ctx.h) // 8, dtype=torch.float64, device="cuda")
+    ybar_h = torch.zeros_like(hist)
+    ctx.synchronize()
+
+    def timed(fn):
+        fn()
+        ctx.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    def fwd():
+        ctx.set_state(st, history=hist)
+        ctx.advance_substage()
+
+    def adj():
+        ctx.set_state(st, history=hist)
+        L.lmvd_adjoint_substage(ctx.h, ybar_s.view(torch.uint8), ybar_h, sb, hb_in)
+
+    f_ms, a_ms = timed(fwd), timed(adj)
+    ctx.close()
+    return {"workload": "%s: %dx%dx%d FP64" % (name, w["nx"], w["ny"], w["nz"]), "forward_ms": f_ms,
+            "adjoint_ms": a_ms, "ratio": a_ms / f_ms,
+            "note": "adjoint_ms includes the forward substage it re-runs to record its tape"}
+
+
 def rel_err(a, b):
     import torch
     return float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
@@ -339,6 +388,8 @@ def run_cuda(args):
                         for k, v in r2["prof"].items() if v[1] > 0},
             "state_rel_l2_vs_headline_after_%d_substages" % (args.warmup + args.steps): errs,
         }
+    if rank == 0 and ws == 1 and not args.no_adjoint:
+        out["adjoint"] = adjoint_ratio(L, args.adjoint_workload, stream)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         rate, cores, desc = oracle_rate(w, 2)
         out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
