@@ -19,8 +19,14 @@ Readings of points the paper leaves open:
      at Greville abscissae of the order-(p+1) space for the m2 equations.
   R3 mass conservation holds in B-coefficient space through the exact bidiagonal D*;
      the curl-free equation is collocated at the interior order-(p+1) Greville points.
-  R4 walls at y = +-1 (no-slip) replace potential matching: Omega2 = 0;
+  R4 bc = "walls": no-slip walls at y = +-1 replace potential matching: Omega2 = 0;
      m2^d = d m2^d/dy = 0; m2^c = 0; <m1> = <m3> = 0; dz/dy = 0; <m2^c>(+1) = 0.
+     bc = "potential": the paper's own conditions (Sec. 4.5, Eq. bc_both, md_bc): the Robin
+     rows k m2 -+ dm2/dy = 0 at y = -1 / +1 (Eq. bc_both times k) for m2^c and m2^d;
+     phi2 = 0 at both ends (Eq. md_bc) as the two remaining m2^d rows; Omega2 = 0;
+     d<m1>/dy = d<m3>/dy = 0; dz/dy = 0; <m2^c>(+1) = 0. The m1, m3 lines of Eq. bc_both
+     are not imposed separately: they follow from Omega2 = 0 and the Robin row for m^d,
+     and from the curl-free construction for m^c wherever rho_t vanishes at the boundary.
   R5 the state holds the B* coefficients of m2^d instead of phi2 = (D^2 - k^2) m2^d;
      phi2 is that operator collocated at the order-(p+1) Greville points 2 .. ny-2.
   R6 start-up: n_startup fixed-point iterations from dz/dt = 0, then the history
@@ -61,6 +67,7 @@ class Config:
     beta_n: float = 0.0
     beta_p: float = -4.0
     n_startup: int = 20
+    bc: str = "walls"          # "walls" | "potential" (reading R4)
 
 
 def _ax0(op, F):
@@ -90,27 +97,53 @@ class Operators:
         An[0, :] = b.Bg[1][0, :]
         An[ny - 1, :] = b.Bg[1][ny - 1, :]
         self.A_neumann = An
+        potential = cfg.bc == "potential"
+        if cfg.bc not in ("walls", "potential"):
+            raise ValueError("bc must be 'walls' or 'potential'")
+        # The per-mode matrices are A(k) = A2 - k^2 A0 + k A1. Potential matching (Eq. bc_both
+        # times k): row 0: k m2(-1) - dm2/dy(-1) = 0, row ny: k m2(+1) + dm2/dy(+1) = 0.
+        # (g*_0 = -1 and g*_ny = +1: clamped knots put the end Greville points on the boundary.)
+        def robin(A2, A0, A1):
+            for r, sgn in ((0, -1.0), (ny, 1.0)):
+                A2[r, :] = sgn * b.Ss[1][r, :]
+                A0[r, :] = 0.0
+                A1[r, :] = b.Ss[0][r, :]
         # m^c system (Eq. COM_fourier + CF_fourier, eliminated for m2^c):
-        #   rows 1..ny-1: (B*'' - k^2 B*)(g*_i) m2 = -B'(g*_i) rho_t ; rows 0, ny: m2(-1) = m2(+1) = 0
+        #   rows 1..ny-1: (B*'' - k^2 B*)(g*_i) m2 = -B'(g*_i) rho_t;
+        #   rows 0, ny: walls m2(-1) = m2(+1) = 0, or the Robin rows
         A2 = b.Ss[2].copy()
         A0 = b.Ss[0].copy()
+        A1 = np.zeros_like(A2)
         for r in (0, ny):
             A2[r, :] = 0.0
             A2[r, r] = 1.0
             A0[r, :] = 0.0
-        self.Amc2, self.Amc0 = A2, A0
-        # m2^d update (Eq. phi_poisson with four no-slip rows):
-        #   rows 2..ny-2: (B*'' - k^2 B*)(g*_i) m2 = phi2-target ; m2(+-1) = dm2/dy(+-1) = 0
+        if potential:
+            robin(A2, A0, A1)
+        self.Amc2, self.Amc0, self.Amc1 = A2, A0, A1
+        # m2^d update (Eq. phi_poisson): rows 2..ny-2: (B*'' - k^2 B*)(g*_i) m2 = phi2-target;
+        #   walls: m2(+-1) = dm2/dy(+-1) = 0 in rows 0, ny and 1, ny-1;
+        #   potential: Robin rows 0, ny; phi2(-1) = 0 in row 1 and phi2(+1) = 0 in row ny-1 (Eq. md_bc)
         A2 = b.Ss[2].copy()
         A0 = b.Ss[0].copy()
+        A1 = np.zeros_like(A2)
         for r in (0, 1, ny - 1, ny):
             A0[r, :] = 0.0
             A2[r, :] = 0.0
-        A2[0, 0] = 1.0
-        A2[ny, ny] = 1.0
-        A2[1, :] = b.Ss[1][0, :]
-        A2[ny - 1, :] = b.Ss[1][ny, :]
-        self.Amd2, self.Amd0 = A2, A0
+        if potential:
+            robin(A2, A0, A1)
+            A2[1, :] = b.Ss[2][0, :]
+            A0[1, :] = b.Ss[0][0, :]
+            A2[ny - 1, :] = b.Ss[2][ny, :]
+            A0[ny - 1, :] = b.Ss[0][ny, :]
+        else:
+            A2[0, 0] = 1.0
+            A2[ny, ny] = 1.0
+            A2[1, :] = b.Ss[1][0, :]
+            A2[ny - 1, :] = b.Ss[1][ny, :]
+        self.Amd2, self.Amd0, self.Amd1 = A2, A0, A1
+        # plane means <m1>, <m3>: Dirichlet rows (walls) or Neumann rows (potential matching)
+        self.A_means = self.A_neumann if potential else self.A_interp
         # plane-mean m2^c (Eq. mc_mean): D* c = -<rho_t>, c(+1) = 0
         Am = np.zeros((ny + 1, ny + 1))
         Am[:ny, :] = b.D
@@ -139,13 +172,13 @@ class Operators:
     def spectral(self, f):
         return to_spec(f, self.cfg.nx, self.cfg.nz)
 
-    def solve_k2(self, A2, A0, rhs):
-        """Per-mode solve of (A2 - k^2 A0) x = rhs over the modes with k != 0."""
+    def solve_k2(self, A2, A0, rhs, A1=None):
+        """Per-mode solve of (A2 - k^2 A0 + k A1) x = rhs over the modes with k != 0."""
         out = np.zeros_like(rhs)
         idx = np.nonzero(self.kmask.ravel())[0]
         r = rhs.reshape(rhs.shape[0], -1)
         o = out.reshape(rhs.shape[0], -1)
-        o[:, idx] = banded.solve_k2(A2, A0, self.k2.ravel()[idx], r[:, idx])
+        o[:, idx] = banded.solve_k2(A2, A0, self.k2.ravel()[idx], r[:, idx], A1)
         return out
 
 
@@ -178,7 +211,7 @@ class Substage:
         ny = self.cfg.ny
         rhs = op.spec(ny + 1)
         rhs[1:ny] = -_ax0(op.Bs[1], rt)[1:ny]
-        m2 = op.solve_k2(op.Amc2, op.Amc0, rhs)
+        m2 = op.solve_k2(op.Amc2, op.Amc0, rhs, op.Amc1)
         # plane mean: D* <m2^c> = -<rho_t>, <m2^c>(+1) = 0
         b = np.zeros(ny + 1, dtype=np.complex128)
         b[:ny] = -rt[:, 0, 0]
@@ -319,24 +352,24 @@ class Substage:
         v[0] = 0
         v[ny - 1] = 0
         om = banded.solve(op.A_interp, v) * op.kmask
-        # plane means: interior values advanced, Dirichlet rows (no-slip)
+        # plane means: interior values advanced; Dirichlet (walls) or Neumann (potential) rows
         mm = []
         for cur, r, pr in ((self.mm1, r_m1, p_m1), (self.mm3, r_m3, p_m3)):
             v = op.Bg[0] @ cur + dt * (al * r + be * pr)
             v[0] = 0
             v[ny - 1] = 0
-            mm.append(banded.solve(op.A_interp, v))
+            mm.append(banded.solve(op.A_means, v))
         # z: interior values advanced with dz/dt^{k_f}, Neumann rows
         v = _ax0(op.Bg[0], self.z + dt * (al * zdot + be * self.zdot_prev))
         v[0] = 0
         v[ny - 1] = 0
         z = banded.solve(op.A_neumann, v) * op.keep
-        # m2^d: phi2 at g*_2..g*_{ny-2} advanced, four no-slip rows
+        # m2^d: phi2 at g*_2..g*_{ny-2} advanced, four boundary rows (no-slip or potential matching)
         phi = _ax0(op.Ss[2], self.m2) - op.k2 * _ax0(op.Ss[0], self.m2)
         v = phi + dt * (al * r_phi + be * p_phi)
         v[:2] = 0
         v[ny - 1:] = 0
-        m2 = op.solve_k2(op.Amd2, op.Amd0, v)
+        m2 = op.solve_k2(op.Amd2, op.Amd0, v, op.Amd1)
         return z, om, m2, mm[0], mm[1]
 
     # ---- public API ------------------------------------------------------------------
