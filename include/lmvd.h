@@ -60,6 +60,13 @@ extern "C" {
  *               arithmetic on the FP32 units (pairs of floats, 48-bit significand, error-free
  *               TwoSum/TwoProd compensation), while every spectral step (collocation, m^c and m2^d
  *               solves, RHS assembly, the RK update and the state) stays FP64.
+ * bc_mode     : boundary rows at y0 and y1. 0 = no-slip walls: Omega2 = 0, m2^d = dm2^d/dy = 0,
+ *               m2^c = 0, <m1> = <m3> = 0, dz/dy = 0, <m2^c>(y1) = 0.
+ *               1 = the paper's potential matching (Sec. 4.5, Eq. bc_both, md_bc) for a domain
+ *               truncated in y: the Robin rows k m2 -+ dm2/dy = 0 at y0 / y1 (Eq. bc_both multiplied
+ *               by k) on m2^c and on m2^d, phi2 = 0 at y0 and y1 as the other two m2^d rows,
+ *               Omega2 = 0, d<m1>/dy = d<m3>/dy = 0, dz/dy = 0, <m2^c>(y1) = 0. Both modes put the
+ *               boundary rows first and last in each per-mode system and factor it without pivoting.
  */
 typedef struct {
   int nx, ny, nz, spline_order;
@@ -70,12 +77,13 @@ typedef struct {
   double beta_n, beta_p;
   int n_startup;
   int precision;
+  int bc_mode;
 } lmvd_config;
 
 typedef struct lmvd_ctx lmvd_ctx;
 
 /* Fill *cfg with the defaults (p = 6, 2 pi periods, walls at -1 and +1, Re = 1000, Sc = Fr = 1,
- * density ratio 3, dt = 1e-3, kf = 4, beta_n = 0, beta_p = -4, n_startup = 20, precision = 0) for
+ * density ratio 3, dt = 1e-3, kf = 4, beta_n = 0, beta_p = -4, n_startup = 20, precision = 0, bc_mode = 0) for
  * the given grid.
  * Returns LMVD_ERR_INVALID_ARG if cfg is NULL. */
 int lmvd_default_config(lmvd_config* cfg, int nx, int ny, int nz);

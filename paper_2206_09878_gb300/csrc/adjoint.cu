@@ -660,7 +660,7 @@ int adjoint_impl(Ctx& c) {
   u.scr0 = A.tS; u.scr1 = A.tS + S; u.scrp = A.tSp;
   LMVD_LAUNCH(c, KC_UPDATE, 0, 0, k_adj_update_om_z, dim3(mblocks(g), 2), TPB, 0, g, A.B0gT, c.lu_interp,
               c.lu_neumann, u);
-  LMVD_LAUNCH(c, KC_UPDATE, 0, 0, k_adj_update_means, 1, 32, 0, g, A.B0gT, c.lu_interp, u);
+  LMVD_LAUNCH(c, KC_UPDATE, 0, 0, k_adj_update_means, 1, 32, 0, g, A.B0gT, c.lu_means, u);
   LMVD_LAUNCH(c, KC_UPDATE, 0, 0, k_adj_update_m2, mblocks(g), TPB, 0, g, A.Ss0T, A.Ss2T, c.lu_md, u);
   // step 5: RHS streams, collocation solves, transforms, products of pass 2
   St7 stw{};

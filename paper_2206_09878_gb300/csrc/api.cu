@@ -129,61 +129,94 @@ int upload_lu(Ctx& c, const BandLU& f, DLU& d) {
   return LMVD_OK;
 }
 
-// Band matrices A2 (k-independent part) and A0 (coefficient of -k^2) of the per-mode systems.
+// Band matrices of the per-mode systems A(k) = A2 - k^2 A0 + k A1: A2 is the k-independent part,
+// A0 the coefficient of -k^2, A1 the coefficient of k (non-zero only in the potential-matching rows).
 struct PerMode {
-  DiagBand A2, A0;
+  DiagBand A2, A0, A1;
 };
 
-// m^c system: rows 0 and ny: m2^c(-1) = m2^c(+1) = 0; rows 1..ny-1: (B*'' - k^2 B*) at g*_i.
-PerMode mc_system(const RowBand& Ss0, const RowBand& Ss2, int K) {
-  const int n = Ss0.rows;
+PerMode per_mode_base(const RowBand& Ss0, const RowBand& Ss2, int K) {
   PerMode p;
   p.A2 = to_diag(Ss2, K);
   p.A0 = to_diag(Ss0, K);
-  for (int r : {0, n - 1}) {
-    for (int q = -K; q <= K; ++q) {
-      int j = r + q;
-      if (j < 0 || j >= n) continue;
-      p.A2.el(r, j) = (q == 0) ? 1.0 : 0.0;
-      p.A0.el(r, j) = 0.0;
+  p.A1 = p.A0;
+  std::fill(p.A1.a.begin(), p.A1.a.end(), 0.0);
+  return p;
+}
+
+// Sets row r of the system to the row vectors (a2, a0, a1) of the order-(p+1) space.
+void set_row(PerMode& p, int r, int K, const RowBand* a2, int r2, const RowBand* a0, int r0, const RowBand* a1,
+             int r1, double s2 = 1.0) {
+  const int n = p.A2.n;
+  for (int q = -K; q <= K; ++q) {
+    const int j = r + q;
+    if (j < 0 || j >= n) continue;
+    p.A2.el(r, j) = a2 ? s2 * a2->at(r2, j) : 0.0;
+    p.A0.el(r, j) = a0 ? a0->at(r0, j) : 0.0;
+    p.A1.el(r, j) = a1 ? a1->at(r1, j) : 0.0;
+  }
+}
+
+// Potential matching (Eq. bc_both times k): row 0: k m2(y0) - dm2/dy(y0) = 0; row n-1: k m2(y1) + dm2/dy(y1)
+// = 0. The clamped order-(p+1) Greville points g*_0 and g*_ny are y0 and y1.
+void robin_rows(PerMode& p, int K, const RowBand& Ss0, const RowBand& Ss1) {
+  const int n = p.A2.n;
+  set_row(p, 0, K, &Ss1, 0, nullptr, 0, &Ss0, 0, -1.0);
+  set_row(p, n - 1, K, &Ss1, n - 1, nullptr, 0, &Ss0, n - 1, 1.0);
+}
+
+// m^c system: rows 1..ny-1: (B*'' - k^2 B*) at g*_i; rows 0 and ny: m2^c(y0) = m2^c(y1) = 0 (walls) or the
+// Robin rows (potential matching).
+PerMode mc_system(const RowBand& Ss0, const RowBand& Ss1, const RowBand& Ss2, int K, int bc_mode) {
+  const int n = Ss0.rows;
+  PerMode p = per_mode_base(Ss0, Ss2, K);
+  if (bc_mode == 1) {
+    robin_rows(p, K, Ss0, Ss1);
+  } else {
+    for (int r : {0, n - 1}) {
+      set_row(p, r, K, nullptr, 0, nullptr, 0, nullptr, 0);
+      p.A2.el(r, r) = 1.0;
     }
   }
   return p;
 }
 
-// m2^d update: rows 0, ny: m2 = 0; rows 1, ny-1: dm2/dy = 0 at -1, +1; rows 2..ny-2: (B*'' - k^2 B*) at g*_i.
-PerMode md_system(const RowBand& Ss0, const RowBand& Ss1, const RowBand& Ss2, int K) {
+// m2^d update: rows 2..ny-2: (B*'' - k^2 B*) at g*_i. Walls: rows 0, ny: m2 = 0; rows 1, ny-1: dm2/dy = 0 at
+// y0, y1. Potential matching: rows 0, ny: Robin; row 1: phi2(y0) = 0; row ny-1: phi2(y1) = 0 (Eq. md_bc).
+PerMode md_system(const RowBand& Ss0, const RowBand& Ss1, const RowBand& Ss2, int K, int bc_mode) {
   const int n = Ss0.rows;
-  PerMode p;
-  p.A2 = to_diag(Ss2, K);
-  p.A0 = to_diag(Ss0, K);
-  for (int r : {0, 1, n - 2, n - 1}) {
-    for (int q = -K; q <= K; ++q) {
-      int j = r + q;
-      if (j < 0 || j >= n) continue;
-      p.A0.el(r, j) = 0.0;
-      double v = 0.0;
-      if (r == 0 || r == n - 1) v = (q == 0) ? 1.0 : 0.0;
-      if (r == 1) v = Ss1.at(0, j);          // derivative at y0
-      if (r == n - 2) v = Ss1.at(n - 1, j);  // derivative at y1
-      p.A2.el(r, j) = v;
+  PerMode p = per_mode_base(Ss0, Ss2, K);
+  if (bc_mode == 1) {
+    robin_rows(p, K, Ss0, Ss1);
+    set_row(p, 1, K, &Ss2, 0, &Ss0, 0, nullptr, 0);
+    set_row(p, n - 2, K, &Ss2, n - 1, &Ss0, n - 1, nullptr, 0);
+  } else {
+    for (int r : {0, n - 1}) {
+      set_row(p, r, K, nullptr, 0, nullptr, 0, nullptr, 0);
+      p.A2.el(r, r) = 1.0;
     }
+    set_row(p, 1, K, &Ss1, 0, nullptr, 0, nullptr, 0);
+    set_row(p, n - 2, K, &Ss1, n - 1, nullptr, 0, nullptr, 0);
   }
   return p;
 }
 
 int factor_per_mode(Ctx& c, const PerMode& pm, int K, DLU& out) {
   std::vector<int> nl, nu;
+  DiagBand pattern = pm.A0;  // union of the non-zero patterns of A0 and A1 (A2 is the other argument)
+  for (size_t i = 0; i < pattern.a.size(); ++i)
+    if (pm.A1.a[i] != 0.0) pattern.a[i] = 1.0;
   try {
-    band_profile(pm.A2, pm.A0, nl, nu);
+    band_profile(pm.A2, pattern, nl, nu);
   } catch (const std::exception&) {
     return LMVD_ERR_UNSUPPORTED;
   }
   const int n = pm.A2.n;
-  double *A2, *A0, *lo, *up, *invd;
+  double *A2, *A0, *A1, *lo, *up, *invd;
   int *dnl, *dnu;
   int e = upload(c, pm.A2.a, &A2);
   if (!e) e = upload(c, pm.A0.a, &A0);
+  if (!e) e = upload(c, pm.A1.a, &A1);
   if (!e) e = upload(c, nl, &dnl);
   if (!e) e = upload(c, nu, &dnu);
   if (e) return e;
@@ -195,7 +228,7 @@ int factor_per_mode(Ctx& c, const PerMode& pm, int K, DLU& out) {
   if (cudaMalloc(&invd, sizeof(double) * (size_t)n * M) != cudaSuccess) return LMVD_ERR_OOM;
   c.small_allocs.push_back(invd);
   LMVD_LAUNCH(c, KC_MISC, 0, 8.0 * n * (2 * K + 1) * M, k_factor, mode_blocks(c.g), TPB_MODE, 0, c.g, n, K, A2, A0,
-              dnl, dnu, lo, up, invd);
+              A1, dnl, dnu, lo, up, invd);
   out = DLU{lo, up, invd, dnl, dnu, n, K, M, 0.0};
   for (int i = 0; i < n; ++i) out.flops_per_mode += 4.0 * (nl[i] + nu[i]) + 2.0;
   return cuda_check(c);
@@ -443,7 +476,7 @@ int advance_impl(Ctx& c, const Tape* tape) {
   LMVD_LAUNCH(c, KC_UPDATE, (c.lu_interp.flops_per_mode + c.lu_neumann.flops_per_mode) * g.M + S * (12.0 * c.B0g.w + 20.0),
               16.0 * 8 * S, k_update_om_z,
               dim3(mode_blocks(g), 2), TPB_MODE, 0, g, c.B0g, c.lu_interp, c.lu_neumann, u);
-  LMVD_LAUNCH(c, KC_UPDATE, 0, 0, k_update_means, 1, 32, 0, g, c.B0g, c.lu_interp, u);
+  LMVD_LAUNCH(c, KC_UPDATE, 0, 0, k_update_means, 1, 32, 0, g, c.B0g, c.lu_means, u);
   {
     const double Sp = (double)(g.ny + 1) * g.M;
     LMVD_LAUNCH(c, KC_UPDATE, c.lu_md.flops_per_mode * g.M + Sp * (8.0 * c.Ss0.w + 10.0),
@@ -484,6 +517,7 @@ bool valid_cfg(const lmvd_config& f) {
   if (!(f.re > 0) || !(f.sc > 0) || !(f.fr > 0) || !(f.rho_heavy > 0) || !(f.rho_light > 0)) return false;
   if (!(f.dt > 0) || f.kf < 0 || f.n_startup < 0) return false;
   if (f.precision != 0 && f.precision != 1) return false;
+  if (f.bc_mode != 0 && f.bc_mode != 1) return false;
   return true;
 }
 
@@ -576,8 +610,10 @@ int lmvd_create(const lmvd_config* cfg, void* stream, lmvd_ctx** out) {
     // per-mode LUs of the m^c and m2^d systems
     const int Ks = std::max({half_width(Ss0), half_width(Ss1), half_width(Ss2)});
     if (Ks > KMAX) throw std::runtime_error("band");
-    if (!err) err = factor_per_mode(c, mc_system(Ss0, Ss2, Ks), Ks, c.lu_mc);
-    if (!err) err = factor_per_mode(c, md_system(Ss0, Ss1, Ss2, Ks), Ks, c.lu_md);
+    if (!err) err = factor_per_mode(c, mc_system(Ss0, Ss1, Ss2, Ks, cfg->bc_mode), Ks, c.lu_mc);
+    if (!err) err = factor_per_mode(c, md_system(Ss0, Ss1, Ss2, Ks, cfg->bc_mode), Ks, c.lu_md);
+    // plane means <m1>, <m3>: Dirichlet rows (walls) or Neumann rows (potential matching)
+    c.lu_means = cfg->bc_mode == 1 ? c.lu_neumann : c.lu_interp;
   } catch (const std::exception&) {
     err = err ? err : LMVD_ERR_UNSUPPORTED;
   }

@@ -130,6 +130,7 @@ struct Ctx {
   DBand B0g, B1g, B2g, Bs[4], Sg0, Sg1, Ss0, Ss2;
   double* dstar = nullptr;  // ny entries: (D* c)_i = dstar[i] (c_{i+1} - c_i)
   DLU lu_interp, lu_neumann, lu_mc, lu_md;
+  DLU lu_means;  // lu_interp (walls) or lu_neumann (potential matching): not owned
   double* A2mc = nullptr; double* A0mc = nullptr; double* A2md = nullptr; double* A0md = nullptr;
   int Kmc = 0, Kmd = 0;
   FFTPlan fx, fz;

@@ -336,10 +336,10 @@ __global__ void k_sanitize(Grid g, int rows, cd* f, int zero_mean) {
 }
 
 // ------------------------------------------------------------------ per-mode factorisation
-// LU (no pivoting) of A(k^2) = A2 - k^2 A0 for every mode with k != 0; A2, A0 in diagonal band storage
-// (half-width K, shared), profile nl/nu shared; factors stored per mode (stride M).
-__global__ void k_factor(Grid g, int n, int K, const double* A2, const double* A0, const int* nl, const int* nu,
-                         double* lo, double* up, double* invd) {
+// LU (no pivoting) of A(k) = A2 - k^2 A0 + k A1 for every mode with k != 0; A2, A0, A1 in diagonal band
+// storage (half-width K, shared), profile nl/nu shared; factors stored per mode (stride M).
+__global__ void k_factor(Grid g, int n, int K, const double* A2, const double* A0, const double* A1, const int* nl,
+                         const int* nu, double* lo, double* up, double* invd) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= (int)g.M) return;
   const size_t M = g.M;
@@ -353,10 +353,11 @@ __global__ void k_factor(Grid g, int n, int K, const double* A2, const double* A
   }
   double k1, k3;
   wavenumbers(g, m, k1, k3);
-  const double k2 = k1 * k1 + k3 * k3;
+  const double k2 = k1 * k1 + k3 * k3, k = sqrt(k2);
   double row[2 * KMAX + 1];
   for (int i = 0; i < n; ++i) {
-    for (int q = 0; q < W; ++q) row[q] = A2[(size_t)i * W + q] - k2 * A0[(size_t)i * W + q];
+    for (int q = 0; q < W; ++q)
+      row[q] = A2[(size_t)i * W + q] - k2 * A0[(size_t)i * W + q] + k * A1[(size_t)i * W + q];
     for (int q = nl[i]; q >= 1; --q) {
       const int c = i - q;
       const double l = row[K - q] * invd[(size_t)c * M + m];

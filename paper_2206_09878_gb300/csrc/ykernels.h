@@ -58,8 +58,8 @@ __global__ void k_bdf(size_t n, double a0, double a1, double a2, double a3, doub
 __global__ void k_backfill(size_t n, double c0, double c1, double c2, const cd* z, const cd* zdot, cd* h0, cd* h1,
                            cd* h2);
 __global__ void k_sanitize(Grid g, int rows, cd* f, int zero_mean);
-__global__ void k_factor(Grid g, int n, int K, const double* A2, const double* A0, const int* nl, const int* nu,
-                         double* lo, double* up, double* invd);
+__global__ void k_factor(Grid g, int n, int K, const double* A2, const double* A0, const double* A1, const int* nl,
+                         const int* nu, double* lo, double* up, double* invd);
 
 // pointwise.cu: physical-space products (Sec. 2.1, 4.3, 5)
 struct EosArgs {

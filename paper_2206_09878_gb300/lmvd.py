@@ -30,7 +30,8 @@ class lmvd_config(ctypes.Structure):
                 ("re", ctypes.c_double), ("sc", ctypes.c_double), ("fr", ctypes.c_double),
                 ("rho_heavy", ctypes.c_double), ("rho_light", ctypes.c_double),
                 ("dt", ctypes.c_double), ("kf", ctypes.c_int), ("beta_n", ctypes.c_double),
-                ("beta_p", ctypes.c_double), ("n_startup", ctypes.c_int), ("precision", ctypes.c_int)]
+                ("beta_p", ctypes.c_double), ("n_startup", ctypes.c_int), ("precision", ctypes.c_int),
+                ("bc_mode", ctypes.c_int)]
 
 
 class LmvdError(RuntimeError):

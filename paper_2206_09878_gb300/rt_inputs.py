@@ -23,6 +23,16 @@ order, Nyquist slots zero):
          no-slip conditions hold; both are rescaled so the sampled rms of m2^d
          and of Omega2 / |k| equal u_rms;
   <m1> = <m3> = 0.
+
+The paper's own single-mode set-up (Sec. 5, its domains V^{3D,1}, V^{3D,2} with W = 1, g = 1) is
+PAPER_RT / rt_paper_state: potential-matching boundaries (bc_mode 1) on [0, 1] x [y0, y1] x [0, 1];
+  z   = (1 + tanh((y - h) / (2 eps))) / 2,  eps = 0.05,
+  h   = 0.05 (cos 2 pi x + cos 2 pi z) + delta  (3D; delta = 0 on [-2, 2], 0.5 on [-3.5, 3.5]),
+  rho_h = 1, rho_l = (1 - At) / (1 + At), Re = 1024, Sc = 1, Fr = 1, dt = 2.5e-4 / sqrt(At);
+  the paper's initial momentum m = -(1/(Re Sc)) grad rho is a gradient, so its divergence-free
+  part is zero: Omega2 = m2^d = <m1> = <m3> = 0, and the curl-free part is what the method's
+  start-up derives from rho_t. The "+ delta" the paper also prints after the z profile is read as
+  part of h only (z must stay in [0, 1]).
 """
 import numpy as np
 
@@ -104,3 +114,32 @@ def rt_state(nx, ny, nz, ratio, width, kmax, eta_rms, u_rms, seed, **_):
     m2 *= u_rms / max(rms(m2, wts), 1e-300)
     om *= u_rms / max(rms(om / kk, wts), 1e-300)
     return dict(z=zhat, om=om, m2=m2, mm1=np.zeros(ny), mm3=np.zeros(ny))
+
+
+# the paper's 3D single-mode Rayleigh-Taylor cases (Sec. 5): (nx, ny, nz, At, y0, y1, delta, steps)
+PAPER_RT = {
+    "rtp32": dict(nx=32, ny=65, nz=32, at=0.5, y0=-2.0, y1=2.0, delta=0.0, steps=5),
+    "rtp128": dict(nx=128, ny=512, nz=128, at=0.5, y0=-2.0, y1=2.0, delta=0.0, steps=10),
+    "rtp128_hi": dict(nx=128, ny=1024, nz=128, at=0.85, y0=-3.5, y1=3.5, delta=0.5, steps=10),
+}
+
+
+def paper_rt_config(nx, ny, nz, at, y0, y1, **_):
+    """Problem constants of the paper's set-up (W = g = 1, Re = 1024, Sc = 1)."""
+    return dict(nx=nx, ny=ny, nz=nz, lx=1.0, lz=1.0, y0=y0, y1=y1, re=1024.0, sc=1.0, fr=1.0, rho_h=1.0,
+                rho_l=(1.0 - at) / (1.0 + at), dt=2.5e-4 / np.sqrt(at), bc="potential")
+
+
+def rt_paper_state(nx, ny, nz, y0, y1, delta, eps=0.05, **_):
+    """dict(z, om, m2, mm1, mm3) of the paper's initial condition (module docstring)."""
+    nxh = nx // 2 + 1
+    x = np.arange(nx) / nx
+    zc = np.arange(nz) / nz
+    h = 0.05 * (np.cos(2 * np.pi * x)[None, :] + np.cos(2 * np.pi * zc)[:, None]) + delta
+    y = y0 + (y1 - y0) * np.arange(ny) / (ny - 1)           # the generator's own anchors
+    zfield = 0.5 * (1.0 + np.tanh((y[:, None, None] - h[None]) / (2 * eps)))
+    zhat = np.fft.rfft2(zfield, axes=(1, 2), norm="forward")
+    zhat[:, nz // 2, :] = 0
+    zhat[:, :, nx // 2] = 0
+    return dict(z=zhat, om=np.zeros((ny, nz, nxh), np.complex128), m2=np.zeros((ny + 1, nz, nxh), np.complex128),
+                mm1=np.zeros(ny), mm3=np.zeros(ny))

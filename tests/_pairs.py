@@ -3,7 +3,7 @@ import numpy as np
 import torch
 
 from oracle.lmvd import Config, Substage
-from paper_2206_09878_gb300.rt_inputs import WORKLOADS, rt_state
+from paper_2206_09878_gb300.rt_inputs import PAPER_RT, WORKLOADS, paper_rt_config, rt_paper_state, rt_state
 
 
 def workload(name, **over):
@@ -23,7 +23,8 @@ def gpu_config(L, cfg, precision=0):
     return L.lmvd_default_config(cfg.nx, cfg.ny, cfg.nz, spline_order=cfg.p, lx=cfg.lx, lz=cfg.lz, y0=cfg.y0,
                                  y1=cfg.y1, re=cfg.re, sc=cfg.sc, fr=cfg.fr, rho_heavy=cfg.rho_h,
                                  rho_light=cfg.rho_l, dt=cfg.dt, kf=cfg.kf, beta_n=cfg.beta_n,
-                                 beta_p=cfg.beta_p, n_startup=cfg.n_startup, precision=precision)
+                                 beta_p=cfg.beta_p, n_startup=cfg.n_startup, precision=precision,
+                                 bc_mode=1 if cfg.bc == "potential" else 0)
 
 
 def to_torch(st, device="cuda"):
@@ -59,5 +60,18 @@ def make_pair(L, name, precision=0, **over):
     cfg = oracle_config(w, **{k: v for k, v in over.items() if k not in WORKLOADS[name]})
     S = Substage(cfg)
     st = rt_state(**w)
+    ctx = L.Context(gpu_config(L, cfg, precision))
+    return S, ctx, st, cfg
+
+
+def make_paper_pair(L, name, precision=0, **over):
+    """The paper's own RT set-up (potential matching, tanh interface with h(x1, x3), zero m^d)."""
+    w = dict(PAPER_RT[name])
+    w.update({k: v for k, v in over.items() if k in w})
+    c = paper_rt_config(**w)
+    c.update({k: v for k, v in over.items() if k not in w})
+    cfg = Config(**c)
+    S = Substage(cfg)
+    st = rt_paper_state(**w)
     ctx = L.Context(gpu_config(L, cfg, precision))
     return S, ctx, st, cfg

@@ -32,15 +32,27 @@ def test_every_declared_symbol_is_exported(lib):
     assert set(declared()) == set(lib.EXPORTED)
 
 
-def test_config_struct_layout_matches(lib):
+def test_config_struct_layout_matches(lib, tmp_path):
+    """ctypes offsets of lmvd_config equal the C compiler's, field by field (host gcc on the header)."""
+    names = [f[0] for f in lib.lmvd_config._fields_]
+    body = "".join('printf("%%s %%zu\\n", "%s", offsetof(lmvd_config, %s));' % (n, n) for n in names)
+    src = tmp_path / "probe.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "lmvd.h"\nint main(void){%s'
+                   'printf("sizeof %%zu\\n", sizeof(lmvd_config));return 0;}\n' % body)
+    exe = tmp_path / "probe"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = dict(l.split() for l in subprocess.run([str(exe)], capture_output=True, text=True).stdout.splitlines())
+    for n in names:
+        assert int(out[n]) == getattr(lib.lmvd_config, n).offset, n
+    assert int(out["sizeof"]) == ctypes.sizeof(lib.lmvd_config)
     cfg = lib.lmvd_default_config(32, 33, 32)
-    assert ctypes.sizeof(cfg) == 128
-    assert (cfg.spline_order, cfg.kf, cfg.n_startup, cfg.precision) == (6, 4, 20, 0)
+    assert (cfg.spline_order, cfg.kf, cfg.n_startup, cfg.precision, cfg.bc_mode) == (6, 4, 20, 0, 0)
     assert cfg.beta_n == 0.0 and cfg.beta_p == -4.0 and abs(cfg.rho_light - 1 / 3) < 1e-16
 
 
 @pytest.mark.parametrize("bad", [dict(nx=7), dict(ny=5), dict(spline_order=3), dict(dt=0.0), dict(re=-1.0),
-                                 dict(y1=-2.0), dict(kf=-1), dict(precision=2)])
+                                 dict(y1=-2.0), dict(kf=-1), dict(precision=2),
+                                 dict(bc_mode=2), dict(bc_mode=-1)])
 def test_invalid_configs_rejected_without_gpu(lib, bad):
     cfg = lib.lmvd_default_config(32, 33, 32)
     for k, v in bad.items():

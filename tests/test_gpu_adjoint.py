@@ -93,11 +93,12 @@ def _gpu_map(L, ctx, cfg, st, hi):
     return {k: v.cpu().numpy() for k, v in so.items()}, unpack(cfg, hout.cpu().numpy(), "hist")
 
 
-@pytest.fixture(scope="module")
-def base(L):
-    """A state and history after start-up and one substage of rt32 (32 x 33 x 32), at stage '."""
-    from _pairs import gpu_config, make_pair, to_torch
-    S, ctx, st, cfg = make_pair(L, "rt32", u_rms=1e-2)
+@pytest.fixture(scope="module", params=["walls", "potential"])
+def base(L, request):
+    """A state and history after start-up and one substage of rt32 (32 x 33 x 32), at stage ', with
+    no-slip walls or the potential-matching boundary rows."""
+    from _pairs import make_pair, to_torch
+    S, ctx, st, cfg = make_pair(L, "rt32", u_rms=1e-2, bc=request.param)
     ctx.set_state(to_torch(st))
     ctx.advance_substage()
     hb = ctx.history_buffer()
