@@ -193,6 +193,21 @@ size_t lmvd_state_bytes(const lmvd_ctx* ctx);
 int lmvd_adjoint_substage(lmvd_ctx* ctx, const void* state_bar_out, const void* history_bar_out,
                           void* state_bar_in, void* history_bar_in);
 
+/* Adjoint of the start-up that lmvd_set_state runs when it is given no history (reading of the paper's
+ * open start-up: n_startup applications of the fixed point from dz/dt = 0, then the history
+ * z - j dt/2 dz/dt, j = 1, 2, 3, dz/dt_prev = dz/dt, RHS_prev = 0). Let x be the context's current state
+ * (z, Omega2, m2^d, means; its history is not read) and y = (x, history) what lmvd_set_state(x, NULL)
+ * produces. Given ybar (a state blob and a history blob, as for lmvd_adjoint_substage; the RHS_prev part
+ * of the history blob is ignored because the start-up sets it to zero), this writes xbar = J(x)^T ybar
+ * into state_bar_in (a state blob), with the inner products of lmvd_adjoint_substage. The call re-runs the
+ * start-up from x, keeping dz/dt before each application (n_startup spectral fields, allocated on the
+ * first call and kept), then differentiates each application from its stored iterate; afterwards the
+ * context holds x with the start-up history, as after lmvd_set_state(x, NULL). Pointers: host or device
+ * memory, caller-owned. Synchronous.
+ * Errors: INVALID_ARG (NULL), UNSUPPORTED (precision 1 or kf > 15), OOM, CUDA. */
+int lmvd_adjoint_startup(lmvd_ctx* ctx, const void* state_bar_out, const void* history_bar_out,
+                         void* state_bar_in);
+
 /* Substage counter s (0 after a start-up). -1 if ctx is NULL. */
 int lmvd_substage_index(const lmvd_ctx* ctx);
 

@@ -8,6 +8,11 @@ substage in reverse order. Memory is bounded by checkpointing: the forward keeps
 `every` substages; the backward recomputes each segment from its checkpoint and runs the adjoints of
 that segment from its last substage back to its first.
 
+`Startup.apply(state, context)` is the start-up of lmvd_set_state without history as a differentiable
+map state -> (state, history); its backward pass calls lmvd_adjoint_startup. Composed,
+`Substages.apply(*Startup.apply(x, ctx), ctx, 0, nsub, every)` differentiates K substages from an
+initial state that has no history.
+
 All arithmetic runs in the library; this module only schedules calls and moves buffers. Gradients are
 with respect to the real inner product of the stored entries (real and imaginary parts as separate
 reals), i.e. the gradient of a real loss with respect to the float64 views.
@@ -40,6 +45,7 @@ def history_blob(hist, s):
 
 
 def set_state(ctx, lay, state, hblob):
+    """hblob None: the start-up runs (lmvd_set_state without history)."""
     u8 = state.contiguous().view(torch.uint8)
     v = {k: u8[o:o + n] for k, (o, n) in lay.off.items()}
     L.lmvd_set_state(ctx.h, v["z"], v["om"], v["m2"], v["mm1"], v["mm3"], hblob)
@@ -101,3 +107,27 @@ class Substages(torch.autograd.Function):
                 ys, yh = xbs, xbh
         ctx.synchronize()
         return ys, yh[16:].view(torch.float64).clone(), None, None, None, None
+
+
+class Startup(torch.autograd.Function):
+    @staticmethod
+    def forward(fctx, state, ctx):
+        lay = Layout(ctx)
+        x = state.detach().contiguous().clone()
+        set_state(ctx, lay, x, None)
+        out_s, out_hb = get_state(ctx, lay, state.device)
+        ctx.synchronize()
+        fctx.saved = (ctx, lay, x, out_hb)
+        return out_s, out_hb[16:].view(torch.float64).clone()
+
+    @staticmethod
+    def backward(fctx, g_state, g_hist):
+        ctx, lay, x, hb = fctx.saved
+        dev = x.device
+        ys = torch.zeros_like(x) if g_state is None else g_state.contiguous().clone()
+        yh = history_blob(torch.zeros((lay.hist_bytes - 16) // 8, dtype=torch.float64, device=dev)
+                          if g_hist is None else g_hist, 0)
+        set_state(ctx, lay, x, hb)   # the state x; lmvd_adjoint_startup re-runs the start-up from it
+        xb = torch.empty_like(x)
+        L.lmvd_adjoint_startup(ctx.h, ys.view(torch.uint8), yh, xb.view(torch.uint8))
+        return xb, None

@@ -40,6 +40,9 @@ struct AdjWork {
   cd *zd, *rz, *rt, *mc[3], *rom, *rphi, *sv[10], *st[7], *tS, *tSp;
   double* rm;
   double *fp, *w[3], *ir, *rho, *md[3], *pb[10];
+  // dz/dt before each start-up application (allocated on the first lmvd_adjoint_startup)
+  cd* iterates = nullptr;
+  int n_iterates = 0;
 };
 
 namespace {
@@ -445,6 +448,17 @@ __global__ void k_adj_bdf(size_t n, double c0, double c1, double c2, double c3, 
   }
 }
 
+// start-up back-fill zh_q = z - c_q zdot (q = 0, 1, 2), zdot_prev = zdot: z += sum zh_q bar, zdot = zdot_prev bar -
+// sum c_q zh_q bar
+__global__ void k_adj_backfill(size_t n, double c0, double c1, double c2, const cd* h0, const cd* h1, const cd* h2,
+                               const cd* zdp, cd* z, cd* zd) {
+  for (size_t o = blockIdx.x * (size_t)blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x) {
+    const cd a = h0[o], b = h1[o], d = h2[o];
+    z[o] = z[o] + (a + b + d);
+    zd[o] = zdp[o] - (c0 * a + c1 * b + c2 * d);
+  }
+}
+
 __global__ void k_add(size_t n, cd* y, const cd* x) {
   for (size_t o = blockIdx.x * (size_t)blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x)
     y[o] = y[o] + x[o];
@@ -616,6 +630,9 @@ void chain_mc_T(Ctx& c, AdjWork& A, double* const* bb, const double* a_tape, int
   eval_T(c, {EvalJob{A.B0gT, A.sv[3], A.zd, acc}});
 }
 
+void fp_step_T(Ctx& c, AdjWork& A, const double* a_tape, double* const* b_tape);
+int pass1_T(Ctx& c, AdjWork& A);
+
 int adjoint_impl(Ctx& c) {
   AdjWork& A = *c.adj;
   const Grid& g = c.g;
@@ -686,22 +703,40 @@ int adjoint_impl(Ctx& c) {
   // final m^c from dz/dt^{kf}: adds to the adjoint of dz/dt^{kf}
   chain_mc_T(c, A, A.pb, A.tape.a[kf], 1);
   // step 3 in reverse: k = kf-1 .. 0, dz/dt^{k+1} = A^{-1} F(-w . b_k) + R_z
-  Fields3RC wc{{c.w[0], c.w[1], c.w[2]}};
-  Fields3R wb{{A.w[0], A.w[1], A.w[2]}};
-  for (int k = kf - 1; k >= 0; --k) {
-    LMVD_LAUNCH(c, KC_MISC, 0, 0, k_add, eblocks(S), 256, 0, S, A.rz, A.zd);
-    solve_T(c, c.lu_interp, A.zd, A.tS);
-    cd* t1[1] = {A.tS};
-    double* lp[1] = {A.pb[5]};
-    f_transpose(c, t1, lp, 1);
-    Fields3RC bk{{A.tape.b[k][0], A.tape.b[k][1], A.tape.b[k][2]}};
-    Fields3R bbw{{A.pb[0], A.pb[1], A.pb[2]}};
-    LMVD_LAUNCH(c, KC_PRODUCTS, 0, 0, k_adj_L, eblocks(n), 256, 0, n, wc, bk, A.pb[5], bbw, wb);
-    chain_mc_T(c, A, A.pb, A.tape.a[k], 0);
-  }
+  for (int k = kf - 1; k >= 0; --k) fp_step_T(c, A, A.tape.a[k], A.tape.b[k]);
   // BDF-like guess: zdot^0 = (a0 z + a1 zh0 + a2 zh1 + a3 zh2) / dt
   LMVD_LAUNCH(c, KC_MISC, 0, 0, k_adj_bdf, eblocks(S), 256, 0, S, a[0] / cf.dt, a[1] / cf.dt, a[2] / cf.dt,
               a[3] / cf.dt, A.zd, A.z, A.zh[0], A.zh[1], A.zh[2]);
+  return pass1_T(c, A);
+}
+
+// adjoint of one fixed-point application dz/dt^{k+1} = A^{-1} F(-w . b_k) + R_z, given the adjoint of
+// dz/dt^{k+1} in A.zd (replaced by the adjoint of dz/dt^k) and the application's tape (a_k, b_k)
+void fp_step_T(Ctx& c, AdjWork& A, const double* a_tape, double* const* b_tape) {
+  const size_t S = (size_t)c.g.ny * c.g.M, n = (size_t)c.g.ny * c.g.P;
+  Fields3RC wc{{c.w[0], c.w[1], c.w[2]}};
+  Fields3R wb{{A.w[0], A.w[1], A.w[2]}};
+  LMVD_LAUNCH(c, KC_MISC, 0, 0, k_add, eblocks(S), 256, 0, S, A.rz, A.zd);
+  solve_T(c, c.lu_interp, A.zd, A.tS);
+  cd* t1[1] = {A.tS};
+  double* lp[1] = {A.pb[5]};
+  f_transpose(c, t1, lp, 1);
+  Fields3RC bk{{b_tape[0], b_tape[1], b_tape[2]}};
+  Fields3R bbw{{A.pb[0], A.pb[1], A.pb[2]}};
+  LMVD_LAUNCH(c, KC_PRODUCTS, 0, 0, k_adj_L, eblocks(n), 256, 0, n, wc, bk, A.pb[5], bbw, wb);
+  chain_mc_T(c, A, A.pb, a_tape, 0);
+}
+
+// adjoint of pass 1 (R_z, rho, f', grad z / rho and m^d on the grid from the state), given the adjoints of
+// R_z (A.rz), f' (A.fp), w (A.w), rho (A.rho), 1/rho (A.ir), m^d on the grid (A.md); accumulates into the
+// state adjoints A.z, A.om, A.m2, A.mm1, A.mm3
+int pass1_T(Ctx& c, AdjWork& A) {
+  const Grid& g = c.g;
+  const lmvd_config& cf = c.cfg;
+  const size_t S = (size_t)g.ny * g.M, Sp = (size_t)(g.ny + 1) * g.M, n = (size_t)g.ny * g.P;
+  Fields3RC mdc{{c.md[0], c.md[1], c.md[2]}};
+  Fields10R pbw{};
+  for (int q = 0; q < 10; ++q) pbw.p[q] = A.pb[q];
   // R_z = A^{-1} F(R_z on the grid)
   solve_T(c, c.lu_interp, A.rz, A.tS);
   {
@@ -729,6 +764,37 @@ int adjoint_impl(Ctx& c) {
   return ce == cudaSuccess ? LMVD_OK : LMVD_ERR_CUDA;
 }
 
+// Adjoint of the start-up (reading R6) from the current state x: the state passes through; the history is
+// zh_q = z - c_q dt zdot, zdot_prev = zdot (c_q = 1/2, 1, 3/2), RHS_prev = 0, with zdot after n_startup
+// applications from 0. Each application's physical fields are re-recorded from its stored iterate.
+int adjoint_startup_impl(Ctx& c) {
+  AdjWork& A = *c.adj;
+  const Grid& g = c.g;
+  const lmvd_config& cf = c.cfg;
+  const size_t S = (size_t)g.ny * g.M, Sp = (size_t)(g.ny + 1) * g.M, P = (size_t)g.ny * g.P;
+  const int ny = g.ny, ns = cf.n_startup;
+  cudaStream_t st = c.stream;
+  int err = startup_record(c, &A.tape, A.iterates);
+  if (err) return err;
+  cudaMemcpyAsync(A.z, A.oz, sizeof(cd) * S, cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(A.om, A.oom, sizeof(cd) * S, cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(A.m2, A.om2, sizeof(cd) * Sp, cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(A.mm1, A.omm1, sizeof(double) * ny, cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(A.mm3, A.omm3, sizeof(double) * ny, cudaMemcpyDeviceToDevice, st);
+  cudaMemsetAsync(A.rz, 0, sizeof(cd) * S, st);
+  for (double* p : {A.fp, A.w[0], A.w[1], A.w[2], A.ir, A.rho, A.md[0], A.md[1], A.md[2]})
+    cudaMemsetAsync(p, 0, sizeof(double) * P, st);
+  const double dt = cf.dt;
+  LMVD_LAUNCH(c, KC_MISC, 0, 0, k_adj_backfill, eblocks(S), 256, 0, S, 0.5 * dt, dt, 1.5 * dt, A.ozh[0], A.ozh[1],
+              A.ozh[2], A.ozdp, A.z, A.zd);
+  for (int j = ns - 1; j >= 0; --j) {
+    err = fp_record(c, A.iterates + (size_t)j * S, A.tape.a[0], A.tape.b[0]);
+    if (err) return err;
+    fp_step_T(c, A, A.tape.a[0], A.tape.b[0]);
+  }
+  return pass1_T(c, A);
+}
+
 int copy_dflt(cudaStream_t st, void* dst, const void* src, size_t bytes) {
   return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, st) == cudaSuccess ? LMVD_OK : LMVD_ERR_CUDA;
 }
@@ -737,6 +803,7 @@ int copy_dflt(cudaStream_t st, void* dst, const void* src, size_t bytes) {
 
 void adj_destroy(Ctx& c) {
   if (!c.adj) return;
+  if (c.adj->iterates) cudaFree(c.adj->iterates);
   for (void* p : c.adj->small) cudaFree(p);
   if (c.adj->arena) cudaFree(c.adj->arena);
   delete c.adj;
@@ -784,6 +851,51 @@ int adjoint_substage(Ctx& c, const void* sbar_out, const void* hbar_out, void* s
   if (!err) { err = copy_dflt(st, hi + off, A.romp, S); off += S; }
   if (!err) { err = copy_dflt(st, hi + off, A.rphip, Sp); off += Sp; }
   if (!err) err = copy_dflt(st, hi + off, A.rmp, 2 * R);
+  if (!err && cudaStreamSynchronize(st) != cudaSuccess) err = LMVD_ERR_CUDA;
+  return err;
+}
+
+// state blob in and out as lmvd_adjoint_substage; history blob: the adjoint of the start-up's history
+// (its RHS_prev part is ignored: the start-up sets RHS_prev = 0)
+int adjoint_startup(Ctx& c, const void* sbar_out, const void* hbar_out, void* sbar_in) {
+  if (c.cfg.precision != 0 || c.cfg.kf > KF_MAX_ADJ) return LMVD_ERR_UNSUPPORTED;
+  int err = adj_setup(c);
+  if (err) return err;
+  AdjWork& A = *c.adj;
+  const Grid& g = c.g;
+  const size_t S = sizeof(cd) * g.ny * g.M, Sp = sizeof(cd) * (g.ny + 1) * g.M, R = sizeof(double) * g.ny;
+  const int ns = c.cfg.n_startup;
+  if (ns > A.n_iterates) {
+    if (A.iterates) cudaFree(A.iterates);
+    A.iterates = nullptr;
+    A.n_iterates = 0;
+    if (cudaMalloc(&A.iterates, S * (size_t)ns) != cudaSuccess) {
+      cudaGetLastError();
+      A.iterates = nullptr;
+      return LMVD_ERR_OOM;
+    }
+    A.n_iterates = ns;
+  }
+  cudaStream_t st = c.stream;
+  const char* so = (const char*)sbar_out;
+  const char* ho = (const char*)hbar_out;
+  err = copy_dflt(st, A.oz, so, S);
+  if (!err) err = copy_dflt(st, A.oom, so + S, S);
+  if (!err) err = copy_dflt(st, A.om2, so + 2 * S, Sp);
+  if (!err) err = copy_dflt(st, A.omm1, so + 2 * S + Sp, R);
+  if (!err) err = copy_dflt(st, A.omm3, so + 2 * S + Sp + R, R);
+  size_t off = 16;
+  for (int q = 0; q < 3 && !err; ++q, off += S) err = copy_dflt(st, A.ozh[q], ho + off, S);
+  if (!err) err = copy_dflt(st, A.ozdp, ho + off, S);
+  if (err) return err;
+  err = adjoint_startup_impl(c);
+  if (err) return err;
+  char* si = (char*)sbar_in;
+  err = copy_dflt(st, si, A.z, S);
+  if (!err) err = copy_dflt(st, si + S, A.om, S);
+  if (!err) err = copy_dflt(st, si + 2 * S, A.m2, Sp);
+  if (!err) err = copy_dflt(st, si + 2 * S + Sp, A.mm1, R);
+  if (!err) err = copy_dflt(st, si + 2 * S + Sp + R, A.mm3, R);
   if (!err && cudaStreamSynchronize(st) != cudaSuccess) err = LMVD_ERR_CUDA;
   return err;
 }

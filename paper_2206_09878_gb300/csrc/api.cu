@@ -399,11 +399,18 @@ void fp_apply(Ctx& c, double* a = nullptr, double* const* b = nullptr) {
   solve_interp(c, {SolveJob{c.sv[3], c.Rz, c.zdot}}, c.lu_interp);
 }
 
-void startup(Ctx& c) {
+// Reading R6: n_startup fixed-point applications from dz/dt = 0, then the Taylor back-fill of the history.
+// tape (optional): records the physical z fields of pass 1; iterates (optional): receives dz/dt before each
+// application, n_startup consecutive spectral fields (the adjoint re-records each application from these).
+void startup(Ctx& c, const Tape* tape = nullptr, cd* iterates = nullptr) {
   const size_t S = (size_t)c.g.ny * c.g.M;
-  physical_pass_1(c);
+  physical_pass_1(c, tape ? tape->zp : nullptr);
   cudaMemsetAsync(c.zdot, 0, sizeof(cd) * S, c.stream);
-  for (int it = 0; it < c.cfg.n_startup; ++it) fp_apply(c);
+  for (int it = 0; it < c.cfg.n_startup; ++it) {
+    if (iterates)
+      cudaMemcpyAsync(iterates + (size_t)it * S, c.zdot, sizeof(cd) * S, cudaMemcpyDeviceToDevice, c.stream);
+    fp_apply(c);
+  }
   const double dt = c.cfg.dt;
   LMVD_LAUNCH(c, KC_MISC, 12.0 * S, 80.0 * S, k_backfill, elem_blocks(S), 256, 0, S, 0.5 * dt, dt, 1.5 * dt, c.z,
               c.zdot, c.zh[0], c.zh[1], c.zh[2]);
@@ -506,6 +513,15 @@ int advance_impl(Ctx& c, const Tape* tape) {
 
 namespace lmvd {
 int advance(Ctx& c, const Tape* tape) { return advance_impl(c, tape); }
+int startup_record(Ctx& c, const Tape* tape, cd* iterates) {
+  startup(c, tape, iterates);
+  return cudaGetLastError() == cudaSuccess ? LMVD_OK : LMVD_ERR_CUDA;
+}
+int fp_record(Ctx& c, const cd* zdot_in, double* a, double* const* b) {
+  cudaMemcpyAsync(c.zdot, zdot_in, sizeof(cd) * c.g.ny * c.g.M, cudaMemcpyDeviceToDevice, c.stream);
+  fp_apply(c, a, b);
+  return cudaGetLastError() == cudaSuccess ? LMVD_OK : LMVD_ERR_CUDA;
+}
 }  // namespace lmvd
 
 namespace {
@@ -815,6 +831,12 @@ size_t lmvd_state_bytes(const lmvd_ctx* h) {
 int lmvd_adjoint_substage(lmvd_ctx* h, const void* sbar_out, const void* hbar_out, void* sbar_in, void* hbar_in) {
   if (!h || !sbar_out || !hbar_out || !sbar_in || !hbar_in) return LMVD_ERR_INVALID_ARG;
   const int e = adjoint_substage(h->c, sbar_out, hbar_out, sbar_in, hbar_in);
+  return e ? latch(h->c, e) : LMVD_OK;
+}
+
+int lmvd_adjoint_startup(lmvd_ctx* h, const void* sbar_out, const void* hbar_out, void* sbar_in) {
+  if (!h || !sbar_out || !hbar_out || !sbar_in) return LMVD_ERR_INVALID_ARG;
+  const int e = adjoint_startup(h->c, sbar_out, hbar_out, sbar_in);
   return e ? latch(h->c, e) : LMVD_OK;
 }
 

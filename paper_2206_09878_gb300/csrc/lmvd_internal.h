@@ -164,8 +164,15 @@ struct Ctx {
 
 // one substage (api.cu); with a tape the physical fields the adjoint needs are kept
 int advance(Ctx& c, const Tape* tape);
+// the start-up of lmvd_set_state without history (api.cu), recording the physical z fields of pass 1 in
+// tape->zp and dz/dt before each fixed-point application in iterates (n_startup spectral fields)
+int startup_record(Ctx& c, const Tape* tape, cd* iterates);
+// one fixed-point application from zdot_in (api.cu), recording its physical fields a and b[3]
+int fp_record(Ctx& c, const cd* zdot_in, double* a, double* const* b);
 // adjoint of one substage (adjoint.cu); blobs as documented for lmvd_adjoint_substage
 int adjoint_substage(Ctx& c, const void* sbar_out, const void* hbar_out, void* sbar_in, void* hbar_in);
+// adjoint of the start-up (adjoint.cu); blobs as documented for lmvd_adjoint_startup
+int adjoint_startup(Ctx& c, const void* sbar_out, const void* hbar_out, void* sbar_in);
 void adj_destroy(Ctx& c);
 
 // Bracket a launch: counts it, and with profiling on records CUDA events around it on the stream.

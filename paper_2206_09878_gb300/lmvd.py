@@ -69,6 +69,7 @@ def _load():
         "lmvd_inverse_transform_noalloc": (I, [I, I, I, P, P, I, P]),
         "lmvd_state_bytes": (S, [P]),
         "lmvd_adjoint_substage": (I, [P, P, P, P, P]),
+        "lmvd_adjoint_startup": (I, [P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -85,7 +86,7 @@ EXPORTED = ("lmvd_default_config", "lmvd_create", "lmvd_destroy", "lmvd_set_stat
             "lmvd_substage_index", "lmvd_synchronize", "lmvd_status", "lmvd_strerror", "lmvd_profile_enable",
             "lmvd_profile_read", "lmvd_kernel_class_name", "lmvd_kernel_launches", "lmvd_inverse_transform",
             "lmvd_forward_transform", "lmvd_inverse_transform_noalloc", "lmvd_state_bytes",
-            "lmvd_adjoint_substage")
+            "lmvd_adjoint_substage", "lmvd_adjoint_startup")
 LMVD_KERNEL_CLASSES = 13
 
 
@@ -215,6 +216,11 @@ def lmvd_state_bytes(h):
 def lmvd_adjoint_substage(h, state_bar_out, history_bar_out, state_bar_in, history_bar_in):
     _check(_lib.lmvd_adjoint_substage(h, _ptr(state_bar_out), _ptr(history_bar_out), _ptr(state_bar_in),
                                       _ptr(history_bar_in)), "lmvd_adjoint_substage")
+
+
+def lmvd_adjoint_startup(h, state_bar_out, history_bar_out, state_bar_in):
+    _check(_lib.lmvd_adjoint_startup(h, _ptr(state_bar_out), _ptr(history_bar_out), _ptr(state_bar_in)),
+           "lmvd_adjoint_startup")
 
 
 # ---------------------------------------------------------------- convenience (still marshalling only)

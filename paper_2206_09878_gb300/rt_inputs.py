@@ -143,3 +143,40 @@ def rt_paper_state(nx, ny, nz, y0, y1, delta, eps=0.05, **_):
     zhat[:, :, nx // 2] = 0
     return dict(z=zhat, om=np.zeros((ny, nz, nxh), np.complex128), m2=np.zeros((ny + 1, nz, nxh), np.complex128),
                 mm1=np.zeros(ny), mm3=np.zeros(ny))
+
+
+def eta_modes(nx, nz, kmax, seed, **_):
+    """The interface modes of rt_state: (kx, kz) pairs, their phases theta_k, and the amplitude a that
+    rt_state gives every mode (the rms rescaling), as numpy arrays."""
+    x = 2 * np.pi * np.arange(nx) / nx
+    zc = 2 * np.pi * np.arange(nz) / nz
+    rng = np.random.default_rng(seed)
+    modes = _band_modes(nx, nz, kmax)
+    theta = rng.uniform(0.0, 2 * np.pi, size=len(modes))
+    eta = np.zeros((nz, nx))
+    for (kx, kz), th in zip(modes, theta):
+        eta += np.cos(kx * x[None, :] + kz * zc[:, None] + th)
+    return np.array(modes), theta, np.sqrt(1.0 / np.mean(eta ** 2))
+
+
+def z_from_eta_torch(amps, modes, theta, nx, ny, nz, ratio, width, **_):
+    """z_hat of rt_state for eta = sum_k amps[k] cos(kx x + kz z + theta_k), written with torch operations
+    so that it is differentiable in amps (a float64 tensor; the result lives on amps' device)."""
+    import torch
+    dev, f64 = amps.device, torch.float64
+    rh, rl = 1.0, 1.0 / ratio
+    x = 2 * np.pi * torch.arange(nx, dtype=f64, device=dev) / nx
+    zc = 2 * np.pi * torch.arange(nz, dtype=f64, device=dev) / nz
+    kx = torch.as_tensor(modes[:, 0], dtype=f64, device=dev)
+    kz = torch.as_tensor(modes[:, 1], dtype=f64, device=dev)
+    th = torch.as_tensor(theta, dtype=f64, device=dev)
+    phase = kx[:, None, None] * x[None, None, :] + kz[:, None, None] * zc[None, :, None] + th[:, None, None]
+    eta = (amps[:, None, None] * torch.cos(phase)).sum(0)
+    y = -1.0 + 2.0 * torch.arange(ny, dtype=f64, device=dev) / (ny - 1)
+    rho = 0.5 * (rh + rl) + 0.5 * (rh - rl) * torch.tanh((y[:, None, None] - eta[None]) / width)
+    zfield = rh / (rh - rl) * (1.0 - rl / rho)
+    zhat = torch.fft.rfft2(zfield, dim=(1, 2), norm="forward")
+    keep = torch.ones(zhat.shape[1:], dtype=f64, device=dev)
+    keep[nz // 2, :] = 0
+    keep[:, nx // 2] = 0
+    return zhat * keep

@@ -6,6 +6,8 @@ substage (Algorithm 2 in oracle/lmvd.py) on 16 seeded directions; J^T ybar comes
 Perturbations are relative to each field's size, so a step h = 1e-6 keeps the truncation error of the
 difference quotient below 1e-11 and its rounding error near 1e-10 of the products compared.
 """
+import zlib
+
 import numpy as np
 import pytest
 import torch
@@ -178,29 +180,36 @@ def test_adjoint_matches_oracle_directional_derivatives(L, base):
 
 
 # Cross blocks of the Jacobian with no identity part, so errors in the nonlinear pieces cannot hide
-# behind the pass-through of z and of the history: (outputs weighted by ybar, inputs perturbed).
+# behind the pass-through of z and of the history: (outputs weighted by ybar, inputs perturbed, step h).
+# Blocks with h = 1e-3 are exactly affine in the perturbed inputs (z <- momentum: with z held, R_z is
+# linear in m^d and the fixed point is affine in R_z; the RK update in RHS_prev and dz/dt_prev; the fixed
+# point, with z held, in the BDF guess): there central differences have no truncation error, and the
+# larger step keeps their rounding error small against the O(1) outputs they move by O(dt).
 CROSS = [
-    ("momentum <- z", {"om", "m2"}, set(), {"z"}, set()),                 # density, gravity, C_ij, u
-    ("z <- momentum", {"z"}, set(), {"om", "m2", "mm1"}, set()),           # advection R_z, m^c
-    ("zdot <- z", set(), {"zdot"}, {"z"}, set()),                          # fixed point, L(z), f'(z)
-    ("rhs <- state", set(), {"r_om", "r_phi", "r_m"}, {"z", "om", "m2", "mm1", "mm3"}, set()),
-    ("means <- momentum", {"mm1", "mm3"}, set(), {"om", "m2"}, set()),    # <C12>, <C23>
-    ("state <- old rhs and zdot", {"z", "om", "m2", "mm1"}, set(), set(), {"r_om", "r_phi", "r_m", "zdot"}),
-    ("zdot <- z history", set(), {"zdot"}, set(), {"z1", "z2", "z3"}),   # BDF guess through the iteration
+    ("momentum <- z", {"om", "m2"}, set(), {"z"}, set(), 1e-6),                 # density, gravity, C_ij, u
+    ("z <- momentum", {"z"}, set(), {"om", "m2", "mm1"}, set(), 1e-3),           # advection R_z, m^c
+    ("zdot <- z", set(), {"zdot"}, {"z"}, set(), 1e-6),                          # fixed point, L(z), f'(z)
+    ("rhs <- state", set(), {"r_om", "r_phi", "r_m"}, {"z", "om", "m2", "mm1", "mm3"}, set(), 1e-6),
+    ("means <- momentum", {"mm1", "mm3"}, set(), {"om", "m2"}, set(), 1e-6),    # <C12>, <C23>
+    ("state <- old rhs and zdot", {"z", "om", "m2", "mm1"}, set(), set(), {"r_om", "r_phi", "r_m", "zdot"}, 1e-3),
+    ("zdot <- z history", set(), {"zdot"}, set(), {"z1", "z2", "z3"}, 1e-3),   # BDF guess through the iteration
 ]
 
 
-@pytest.mark.parametrize("name,ys_keys,yh_keys,xs_keys,xh_keys", CROSS, ids=[c[0] for c in CROSS])
-def test_adjoint_cross_blocks(L, base, name, ys_keys, yh_keys, xs_keys, xh_keys):
+def _seed(name):
+    return zlib.crc32(name.encode())
+
+
+@pytest.mark.parametrize("name,ys_keys,yh_keys,xs_keys,xh_keys,h", CROSS, ids=[c[0] for c in CROSS])
+def test_adjoint_cross_blocks(L, base, name, ys_keys, yh_keys, xs_keys, xh_keys, h):
     S, ctx, cfg, xs, xh = base
-    rng = np.random.default_rng(abs(hash(name)) % (2 ** 31))
+    rng = np.random.default_rng(_seed(name))
     ys, yh = _gpu_map(L, ctx, cfg, xs, xh)
     ybs = {k: (v if k in ys_keys else 0 * v) for k, v in _random_like(rng, cfg, ys, True).items()}
     ybh = {k: (v if k in yh_keys else 0 * v) for k, v in _random_like(rng, cfg, yh, False).items()}
     dxs = {k: (v if k in xs_keys else 0 * v) for k, v in _random_like(rng, cfg, xs, True).items()}
     dxh = {k: (v if k in xh_keys else 0 * v) for k, v in _random_like(rng, cfg, xh, False).items()}
     xbs, xbh = _adjoint(L, ctx, cfg, xs, xh, ybs, ybh)
-    h = 1e-6
     pp = _gpu_map(L, ctx, cfg, {k: xs[k] + h * dxs[k] for k in xs}, {k: xh[k] + h * dxh[k] for k in xh})
     mm = _gpu_map(L, ctx, cfg, {k: xs[k] - h * dxs[k] for k in xs}, {k: xh[k] - h * dxh[k] for k in xh})
     lhs = dot(ybs, {k: (pp[0][k] - mm[0][k]) / (2 * h) for k in xs}) + \
@@ -208,3 +217,81 @@ def test_adjoint_cross_blocks(L, base, name, ys_keys, yh_keys, xs_keys, xh_keys)
     rhs = dot(xbs, dxs) + dot(xbh, dxh)
     assert abs(rhs) > 0
     assert abs(lhs - rhs) <= 1e-5 * max(abs(lhs), abs(rhs)), (name, lhs, rhs)
+
+
+# ---- the start-up of lmvd_set_state without history: x -> (x, history), reading R6
+def _startup_map(L, ctx, cfg, st):
+    dev = {k: torch.from_numpy(np.ascontiguousarray(v)).cuda() for k, v in st.items()}
+    ctx.set_state(dev)
+    hout = ctx.history_buffer()
+    so = ctx.get_state(history=hout)
+    ctx.synchronize()
+    return {k: v.cpu().numpy() for k, v in so.items()}, unpack(cfg, hout.cpu().numpy(), "hist")
+
+
+def _startup_adjoint(L, ctx, cfg, x_state, yb_state, yb_hist):
+    dev = {k: torch.from_numpy(np.ascontiguousarray(v)).cuda() for k, v in x_state.items()}
+    ctx.set_state(dev)
+    sbi = torch.zeros(L.lmvd_state_bytes(ctx.h), dtype=torch.uint8, device="cuda")
+    sbo = torch.from_numpy(pack(cfg, yb_state, "state")).cuda()
+    hbo = torch.from_numpy(pack(cfg, yb_hist, "hist")).cuda()
+    L.lmvd_adjoint_startup(ctx.h, sbo, hbo, sbi)
+    return unpack(cfg, sbi.cpu().numpy(), "state")
+
+
+# (weighted outputs: state keys, history keys; perturbed state keys); the history-only blocks have no
+# identity part (the state passes through the start-up unchanged)
+STARTUP_BLOCKS = [
+    ("all", {"z", "om", "m2", "mm1", "mm3"}, {"z1", "z2", "z3", "zdot"}, {"z", "om", "m2", "mm1", "mm3"}),
+    ("history <- z", set(), {"z1", "z2", "z3", "zdot"}, {"z"}),
+    ("history <- momentum", set(), {"z1", "z2", "z3", "zdot"}, {"om", "m2", "mm1", "mm3"}),
+]
+
+
+@pytest.mark.parametrize("name,ys_keys,yh_keys,xs_keys", STARTUP_BLOCKS, ids=[b[0] for b in STARTUP_BLOCKS])
+def test_startup_adjoint_matches_gpu_central_differences(L, base, name, ys_keys, yh_keys, xs_keys):
+    S, ctx, cfg, xs, _ = base
+    rng = np.random.default_rng(_seed("startup " + name))
+    ys, yh = _startup_map(L, ctx, cfg, xs)
+    ybs = {k: (v if k in ys_keys else 0 * v) for k, v in _random_like(rng, cfg, ys, True).items()}
+    ybh = {k: (v if k in yh_keys else 0 * v) for k, v in _random_like(rng, cfg, {**yh, **{
+        q: np.ones_like(yh[q]) for q in ("r_om", "r_phi", "r_m")}}, False).items()}
+    dxs = {k: (v if k in xs_keys else 0 * v) for k, v in _random_like(rng, cfg, xs, True).items()}
+    xbs = _startup_adjoint(L, ctx, cfg, xs, ybs, ybh)
+    h = 1e-6
+    pp = _startup_map(L, ctx, cfg, {k: xs[k] + h * dxs[k] for k in xs})
+    mm = _startup_map(L, ctx, cfg, {k: xs[k] - h * dxs[k] for k in xs})
+    lhs = dot(ybs, {k: (pp[0][k] - mm[0][k]) / (2 * h) for k in xs}) + \
+        dot(ybh, {k: (pp[1][k] - mm[1][k]) / (2 * h) for k in yh})
+    rhs = dot(xbs, dxs)
+    assert abs(rhs) > 0
+    assert abs(lhs - rhs) <= 1e-6 * max(abs(lhs), abs(rhs)), (name, lhs, rhs)
+
+
+def test_startup_adjoint_matches_oracle_directional_derivatives(L, base):
+    """16 seeded directions: <J^T ybar, dx> (GPU) against the oracle's start-up by central differences."""
+    S, ctx, cfg, xs, _ = base
+    rng = np.random.default_rng(3100)
+
+    def oracle_map(st):
+        S.set_state(st["z"], st["om"], st["m2"], st["mm1"], st["mm3"])
+        h2 = S.history()
+        return S.state(), dict(z1=h2["z1"], z2=h2["z2"], z3=h2["z3"], zdot=h2["zdot"])
+
+    ys, yh = oracle_map(xs)
+    ybs = _random_like(rng, cfg, ys, True)
+    ybh = _random_like(rng, cfg, yh, False)
+    full_h = dict(ybh, r_om=np.zeros(ys["om"].shape, complex), r_phi=np.zeros(ys["m2"].shape, complex),
+                  r_m=np.zeros(2 * cfg.ny))
+    xbs = _startup_adjoint(L, ctx, cfg, xs, ybs, full_h)
+    h = 1e-6
+    worst = 0.0
+    for _ in range(16):
+        dxs = _random_like(rng, cfg, xs, True)
+        pp = oracle_map({k: xs[k] + h * dxs[k] for k in xs})
+        mm = oracle_map({k: xs[k] - h * dxs[k] for k in xs})
+        lhs = dot(ybs, {k: (pp[0][k] - mm[0][k]) / (2 * h) for k in xs}) + \
+            dot(ybh, {k: (pp[1][k] - mm[1][k]) / (2 * h) for k in yh})
+        rhs = dot(xbs, dxs)
+        worst = max(worst, abs(lhs - rhs) / max(abs(lhs), abs(rhs)))
+    assert worst <= 1e-6, worst
