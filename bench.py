@@ -325,7 +325,62 @@ def adjoint_ratio(L, name, stream, reps=3):
     ctx.close()
     return {"workload": "%s: %dx%dx%d FP64" % (name, w["nx"], w["ny"], w["nz"]), "forward_ms": f_ms,
             "adjoint_ms": a_ms, "ratio": a_ms / f_ms,
-            "note": "adjoint_ms includes the forward substage it re-runs to record its tape"}
+            "note": "adjoint_ms includes the forward substage it re-runs to record its tape",
+            "gradient": gradient_ratio(L, name, stream)}
+
+
+def gradient_ratio(L, name, stream, rk_steps=20, every_steps=5):
+    """The whole gradient of the adjoint configuration against its forward: start-up (n_startup = 20) and
+    2 rk_steps substages from an initial state without history; the gradient runs that forward keeping a
+    checkpoint every every_steps RK steps, then the adjoints (recomputing each segment) and the start-up
+    adjoint. CUDA events on the library stream, on which the torch operations of the chain also run."""
+    import numpy as np
+    import torch
+
+    from paper_2206_09878_gb300.autograd import Layout, Startup, Substages, state_from_dict
+    from paper_2206_09878_gb300.rt_inputs import rt_state
+    w, _ = workload_config(name)
+    cfg = L.lmvd_default_config(w["nx"], w["ny"], w["nz"], re=w["re"], rho_light=1.0 / w["ratio"], dt=w["dt"])
+    ctx = L.Context(cfg, stream=stream)
+    nsub, every = 2 * rk_steps, 2 * every_steps
+    with torch.cuda.stream(stream):
+        x0 = state_from_dict({k: torch.from_numpy(np.ascontiguousarray(v)).cuda() for k, v in rt_state(**w).items()})
+        lay = Layout(ctx)
+        weight = torch.from_numpy(np.random.default_rng(0).normal(size=x0.numel())).cuda()
+
+        def fwd():
+            ctx.set_state({k: v for k, v in zip(("z", "om", "m2", "mm1", "mm3"), split(x0))})
+            for _ in range(nsub):
+                ctx.advance_substage()
+
+        def split(x):
+            u8 = x.view(torch.uint8)
+            out = []
+            for k in ("z", "om", "m2", "mm1", "mm3"):
+                o, n = lay.off[k]
+                out.append(u8[o:o + n])
+            return out
+
+        def grad():
+            x = x0.clone().requires_grad_(True)
+            s, h = Substages.apply(*Startup.apply(x, ctx), ctx, 0, nsub, every)
+            (weight * s).sum().backward()
+
+        def timed(fn):
+            fn()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1)
+
+        f_ms, g_ms = timed(fwd), timed(grad)
+    ctx.close()
+    return {"substages": nsub, "checkpoint_every_substages": every, "n_startup": cfg.n_startup,
+            "forward_ms": f_ms, "gradient_ms": g_ms, "ratio": g_ms / f_ms,
+            "note": "gradient_ms = forward with checkpoints + adjoints with segment recomputation + start-up adjoint"}
 
 
 def rel_err(a, b):
