@@ -605,7 +605,9 @@ void eval_T(Ctx& c, std::initializer_list<EvalJob> jobs) {
   EvalJobs ej{};
   int n = 0;
   for (const EvalJob& j : jobs) ej.j[n++] = j;
-  LMVD_LAUNCH(c, KC_EVAL, 0, 0, k_eval, dim3(mblocks(c.g), n), TPB, 0, c.g, ej);
+  int maxrows = 0;
+  for (int q = 0; q < n; ++q) maxrows = std::max(maxrows, ej.j[q].B.rows);
+  LMVD_LAUNCH(c, KC_EVAL, 0, 0, k_eval, dim3(mblocks(c.g), n, row_chunks(c.g, maxrows)), TPB, 0, c.g, ej);
 }
 
 // adjoint of: a = G(B0 zdot); rt = A^{-1} F(f' a); m^c = C(rt); b = G(E m^c), given bbar (3 physical

@@ -69,6 +69,7 @@ void prof_collect(Ctx& c) {
 constexpr int TPB_MODE = 128;
 
 unsigned mode_blocks(const Grid& g) { return (unsigned)((g.M + TPB_MODE - 1) / TPB_MODE); }
+
 unsigned elem_blocks(size_t n) {
   size_t b = (n + 255) / 256;
   return (unsigned)std::min<size_t>(b, 152 * 32);
@@ -296,7 +297,10 @@ void eval_jobs(Ctx& c, std::initializer_list<EvalJob> jobs) {
     rows += 2.0 * j.B.rows;
     fl += 4.0 * j.B.rows * j.B.w;
   }
-  LMVD_LAUNCH(c, KC_EVAL, fl * c.g.M, 16.0 * rows * c.g.M, k_eval, dim3(mode_blocks(c.g), n), TPB_MODE, 0, c.g, ej);
+  int maxrows = 0;
+  for (int q = 0; q < n; ++q) maxrows = std::max(maxrows, ej.j[q].B.rows);
+  LMVD_LAUNCH(c, KC_EVAL, fl * c.g.M, 16.0 * rows * c.g.M, k_eval,
+              dim3(mode_blocks(c.g), n, row_chunks(c.g, maxrows)), TPB_MODE, 0, c.g, ej);
 }
 
 void solve_interp(Ctx& c, std::initializer_list<SolveJob> jobs, const DLU& lu) {
@@ -323,7 +327,8 @@ void physical_pass_1(Ctx& c, double* const* zp = nullptr) {
   for (int f = 0; f < 8; ++f) o.p[f] = c.sv[f];
   const double SM = (double)c.g.ny * c.g.M;
   LMVD_LAUNCH(c, KC_EVAL_P1, SM * (4.0 * 6 * c.B0g.w + 20.0), 16.0 * SM * 11 + 16.0 * c.g.M, k_eval_p1,
-              mode_blocks(c.g), TPB_MODE, 0, c.g, c.B0g, c.B1g, c.B2g, c.Sg0, c.Sg1, c.z, c.om, c.m2, c.mm1, c.mm3, o);
+              dim3(mode_blocks(c.g), row_chunks(c.g, c.g.ny)), TPB_MODE, 0, c.g, c.B0g, c.B1g, c.B2g, c.Sg0, c.Sg1,
+              c.z, c.om, c.m2, c.mm1, c.mm3, o);
   // physical: z, zx, zz, zy, lapz -> pw[0..4]; m^d -> md[0..2]
   cd* in[8] = {c.sv[0], c.sv[1], c.sv[2], c.sv[3], c.sv[4], c.sv[5], c.sv[6], c.sv[7]};
   double* out[8] = {zf[0], zf[1], zf[2], zf[3], zf[4], c.md[0], c.md[1], c.md[2]};
@@ -468,7 +473,8 @@ int advance_impl(Ctx& c, const Tape* tape) {
                c.lu_interp);
   Fields7C stc{};
   for (int f = 0; f < 7; ++f) stc.p[f] = c.st[f];
-  LMVD_LAUNCH(c, KC_RHS_EVAL, S * (4.0 * 6 * c.B1g.w + 4.0), 16.0 * 9 * S, k_rhs_eval, mode_blocks(g), TPB_MODE, 0,
+  LMVD_LAUNCH(c, KC_RHS_EVAL, S * (4.0 * 6 * c.B1g.w + 4.0), 16.0 * 9 * S, k_rhs_eval,
+              dim3(mode_blocks(g), row_chunks(g, g.ny + 1)), TPB_MODE, 0,
               g, c.B1g, c.B2g, c.Bs[0], c.Bs[1], c.Bs[2], c.Bs[3], stc, c.r_om, c.r_phi, c.r_m);
   // step 6: midpoint RK2, low-storage: (al, be) = (1/2, 0) at stage n, (1, -1/2) at stage '
   UpdateArgs u{};

@@ -66,6 +66,21 @@ __device__ inline void wavenumbers(const Grid& g, int m, double& k1, double& k3)
   k3 = 6.283185307179586476925286766559 / g.lz * kz;
 }
 
+// Rows [r0, r1) of chunk c out of nc over `rows` rows (contiguous, sizes differing by at most one).
+__host__ __device__ inline void row_range(int rows, int c, int nc, int& r0, int& r1) {
+  r0 = (int)((long long)rows * c / nc);
+  r1 = (int)((long long)rows * (c + 1) / nc);
+}
+
+// Row chunks for the evaluation kernels: enough threads for about 1024 per SM when the grid has few
+// Fourier modes, at least 8 rows per thread.
+inline unsigned row_chunks(const Grid& g, int rows) {
+  const size_t want = ((size_t)152 * 1024 + g.M - 1) / g.M;
+  const size_t cap = (size_t)(rows / 8 > 1 ? rows / 8 : 1);
+  const size_t ch = want < cap ? want : cap;
+  return (unsigned)(ch > 1 ? ch : 1);
+}
+
 __device__ inline cd band_row(const DBand& B, int i, const cd* x, size_t M, int m) {
   const int c = B.c0[i];
   const double* v = B.v + (size_t)i * B.w;

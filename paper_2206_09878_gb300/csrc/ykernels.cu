@@ -13,13 +13,17 @@ namespace lmvd {
 // out[0..7] = z, dz/dx, dz/dz, dz/dy, lap z, m1^d, m2^d, m3^d at the Greville points of the order-p space.
 // m1^d, m3^d follow Eq. md_recon with d m2^d / dy evaluated directly from the order-(p+1) space;
 // the k = 0 mode carries the plane means (and m2^d = 0).
+// Rows are split into gridDim.y chunks (row_range), so that a grid with few modes still has enough
+// threads, each with its own loads in flight.
 __global__ void k_eval_p1(Grid g, DBand B0g, DBand B1g, DBand B2g, DBand Sg0, DBand Sg1, const cd* z,
                           const cd* om, const cd* m2, const double* mm1, const double* mm3, Fields8 out) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= (int)g.M) return;
   const size_t M = g.M;
+  int r0, r1;
+  row_range(g.ny, blockIdx.y, gridDim.y, r0, r1);
   if (is_nyquist(g, m)) {
-    for (int i = 0; i < g.ny; ++i)
+    for (int i = r0; i < r1; ++i)
       for (int f = 0; f < 8; ++f) out.p[f][(size_t)i * M + m] = mk(0, 0);
     return;
   }
@@ -27,7 +31,7 @@ __global__ void k_eval_p1(Grid g, DBand B0g, DBand B1g, DBand B2g, DBand Sg0, DB
   wavenumbers(g, m, k1, k3);
   const double k2 = k1 * k1 + k3 * k3;
   const double ik2 = m == 0 ? 0.0 : 1.0 / k2;
-  for (int i = 0; i < g.ny; ++i) {
+  for (int i = r0; i < r1; ++i) {
     const size_t o = (size_t)i * M + m;
     const cd zg = band_row(B0g, i, z, M, m);
     const cd zy = band_row(B1g, i, z, M, m);
@@ -52,19 +56,22 @@ __global__ void k_eval_p1(Grid g, DBand B0g, DBand B1g, DBand B2g, DBand Sg0, DB
 }
 
 // ------------------------------------------------------------------ generic values at points
-// job blockIdx.y: out = B in (or out += B in), rows B.rows; Nyquist modes zero (or unchanged).
+// job blockIdx.y: out = B in (or out += B in), rows B.rows split into gridDim.z chunks; Nyquist modes
+// zero (or unchanged).
 __global__ void k_eval(Grid g, EvalJobs jobs) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= (int)g.M) return;
   const EvalJob& jb = jobs.j[blockIdx.y];
   const size_t M = g.M;
   const bool ny = is_nyquist(g, m);
+  int r0, r1;
+  row_range(jb.B.rows, blockIdx.z, gridDim.z, r0, r1);
   if (jb.acc) {
     if (ny) return;
-    for (int i = 0; i < jb.B.rows; ++i) jb.out[(size_t)i * M + m] = jb.out[(size_t)i * M + m] + band_row(jb.B, i, jb.in, M, m);
+    for (int i = r0; i < r1; ++i) jb.out[(size_t)i * M + m] = jb.out[(size_t)i * M + m] + band_row(jb.B, i, jb.in, M, m);
     return;
   }
-  for (int i = 0; i < jb.B.rows; ++i)
+  for (int i = r0; i < r1; ++i)
     jb.out[(size_t)i * M + m] = ny ? mk(0, 0) : band_row(jb.B, i, jb.in, M, m);
 }
 
@@ -180,27 +187,33 @@ __global__ void k_rhs_combine(Grid g, double mu, double grav, Fields10C sv, Fiel
 
 // RHS values from the streams (st1..st6 now B coefficients): R_Omega2 at g (ny rows), R_phi2 at g*
 // (ny + 1 rows), and for k = 0 the mean RHS (2 ny reals).
+// Rows 0..ny (R_phi2 has ny + 1) are split into gridDim.y chunks.
 __global__ void k_rhs_eval(Grid g, DBand B1g, DBand B2g, DBand Bs0, DBand Bs1, DBand Bs2, DBand Bs3, Fields7C st,
                            cd* r_om, cd* r_phi, double* r_m) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= (int)g.M) return;
   const size_t M = g.M;
   const int ny = g.ny;
+  int r0, r1;
+  row_range(ny + 1, blockIdx.y, gridDim.y, r0, r1);
   if (m == 0 || is_nyquist(g, m)) {
-    for (int i = 0; i < ny; ++i) r_om[(size_t)i * M + m] = mk(0, 0);
-    for (int i = 0; i <= ny; ++i) r_phi[(size_t)i * M + m] = mk(0, 0);
-    if (m == 0)
-      for (int i = 0; i < ny; ++i) {
+    for (int i = r0; i < r1; ++i) {
+      if (i < ny) r_om[(size_t)i * M + m] = mk(0, 0);
+      r_phi[(size_t)i * M + m] = mk(0, 0);
+      if (m == 0 && i < ny) {
         r_m[i] = (band_row(B1g, i, st.p[1], M, 0) + band_row(B2g, i, st.p[2], M, 0)).re;
         r_m[ny + i] = (band_row(B1g, i, st.p[4], M, 0) + band_row(B2g, i, st.p[5], M, 0)).re;
       }
+    }
     return;
   }
-  for (int i = 0; i < ny; ++i)
-    r_om[(size_t)i * M + m] = st.p[0][(size_t)i * M + m] + band_row(B1g, i, st.p[1], M, m) + band_row(B2g, i, st.p[2], M, m);
-  for (int i = 0; i <= ny; ++i)
+  for (int i = r0; i < r1; ++i) {
+    if (i < ny)
+      r_om[(size_t)i * M + m] = st.p[0][(size_t)i * M + m] + band_row(B1g, i, st.p[1], M, m) +
+                                band_row(B2g, i, st.p[2], M, m);
     r_phi[(size_t)i * M + m] = band_row(Bs0, i, st.p[3], M, m) + band_row(Bs1, i, st.p[4], M, m) +
                                band_row(Bs2, i, st.p[5], M, m) + band_row(Bs3, i, st.p[6], M, m);
+  }
 }
 
 // ------------------------------------------------------------------ RK2 update (step 6)
