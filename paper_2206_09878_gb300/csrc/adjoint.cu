@@ -78,22 +78,33 @@ __global__ void k_wscale(Grid g, FieldsW10 f, double s0, double s1) {
   }
 }
 
-// out = A^{-T} in for shared factors; blockIdx.y selects the job
-__global__ void k_solve_shared_T(Grid g, DLU lu, SolveJobs jobs) {
-  const int m = blockIdx.x * blockDim.x + threadIdx.x;
-  if (m >= (int)g.M) return;
-  const SolveJob& jb = jobs.j[blockIdx.y];
+// out = A^{-T} in for job blockIdx.y, shared or per-mode factors; rows of the result outside [zlo, zhi]
+// are zero (boundary rows whose forward right-hand side is a constant). out may alias in. Nyquist modes
+// are set to zero. k_solve_T_cd: one thread per mode; k_solve_T_re: one thread per (mode, real part).
+struct SolveTJob {
+  const cd* in;
+  cd* out;
+  int zlo, zhi;
+};
+struct SolveTJobs {
+  SolveTJob j[8];
+};
+template <class V>
+__device__ void solve_T_job(const Grid& g, const DLU& lu, const SolveTJob& jb) {
+  constexpr int TPM = sizeof(V) == sizeof(cd) ? 1 : 2;
+  const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (t >= TPM * g.M) return;
+  const int m = (int)(t / TPM), comp = (int)(t % TPM);
   const size_t M = g.M;
+  V* out = reinterpret_cast<V*>(jb.out);
   if (is_nyquist(g, m)) {
-    for (int i = 0; i < lu.n; ++i) jb.out[(size_t)i * M + m] = mk(0, 0);
+    for (int i = 0; i < lu.n; ++i) out[vidx<V>(i, M, m, comp)] = vzero<V>();
     return;
   }
-  const cd* in = jb.in;
-  cd* out = jb.out;
-  band_solve_T(
-      lu, m, out, M, [&](int i) { return in[(size_t)i * M + m]; },
-      [&](int i, cd x, cd) { out[(size_t)i * M + m] = x; });
+  band_solve_T_v<V>(lu, m, comp, reinterpret_cast<const V*>(jb.in), out, M, jb.zlo, jb.zhi);
 }
+__global__ void k_solve_T_cd(Grid g, DLU lu, SolveTJobs jobs) { solve_T_job<cd>(g, lu, jobs.j[blockIdx.y]); }
+__global__ void k_solve_T_re(Grid g, DLU lu, SolveTJobs jobs) { solve_T_job<double>(g, lu, jobs.j[blockIdx.y]); }
 
 // ------------------------------------------------------------------ update (step 6) adjoint
 struct AdjUpd {
@@ -106,20 +117,19 @@ struct AdjUpd {
   cd* scrp;         // ny + 1 rows
 };
 
-__global__ void k_adj_update_om_z(Grid g, DBand B0gT, DLU lu_i, DLU lu_n, AdjUpd a) {
+// After the transposed solves v = A^{-T} ybar (boundary rows zero; scr0 for Omega2 with the interpolation
+// LU, scr1 for z with the Neumann LU): transposed evaluation and the RK coefficients. Rows split over
+// gridDim.y chunks, job blockIdx.z (0: Omega2, 1: z).
+__global__ void k_adj_update_om_z_post(Grid g, DBand B0gT, AdjUpd a) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= (int)g.M || is_nyquist(g, m)) return;
   const size_t M = g.M;
-  const int ny = g.ny;
-  const int job = blockIdx.y;
+  const int job = blockIdx.z;
   if (job == 0 && m == 0) return;  // Omega2 has no k = 0 mode
-  const DLU& lu = job == 0 ? lu_i : lu_n;
-  const cd* ybar = job == 0 ? a.oom : a.oz;
-  cd* v = job == 0 ? a.scr0 : a.scr1;
-  band_solve_T(
-      lu, m, v, M, [&](int i) { return ybar[(size_t)i * M + m]; },
-      [&](int i, cd x, cd) { v[(size_t)i * M + m] = (i == 0 || i == ny - 1) ? mk(0, 0) : x; });
-  for (int j = 0; j < ny; ++j) {
+  const cd* v = job == 0 ? a.scr0 : a.scr1;
+  int r0, r1;
+  row_range(g.ny, blockIdx.y, gridDim.y, r0, r1);
+  for (int j = r0; j < r1; ++j) {
     const size_t o = (size_t)j * M + m;
     const cd t = band_row(B0gT, j, v, M, m);
     if (job == 0) {
@@ -133,7 +143,6 @@ __global__ void k_adj_update_om_z(Grid g, DBand B0gT, DLU lu_i, DLU lu_n, AdjUpd
     }
   }
 }
-
 __global__ void k_adj_update_means(Grid g, DBand B0gT, DLU lu, AdjUpd a) {
   const int c = threadIdx.x;
   if (c > 1) return;
@@ -172,19 +181,19 @@ __global__ void k_adj_update_means(Grid g, DBand B0gT, DLU lu, AdjUpd a) {
   }
 }
 
-__global__ void k_adj_update_m2(Grid g, DBand Ss0T, DBand Ss2T, DLU lu, AdjUpd a) {
+// After v = A^{-T} m2^d-bar (per-mode factors, rows < 2 and > ny - 2 zero) in scrp: transposed phi2
+// evaluation and the RK coefficients. Rows 0..ny split over gridDim.y chunks.
+__global__ void k_adj_update_m2_post(Grid g, DBand Ss0T, DBand Ss2T, AdjUpd a) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= (int)g.M || m == 0 || is_nyquist(g, m)) return;
   const size_t M = g.M;
-  const int ny = g.ny;
   double k1, k3;
   wavenumbers(g, m, k1, k3);
   const double k2 = k1 * k1 + k3 * k3;
-  cd* v = a.scrp;
-  band_solve_T(
-      lu, m, v, M, [&](int i) { return a.om2[(size_t)i * M + m]; },
-      [&](int i, cd x, cd) { v[(size_t)i * M + m] = (i < 2 || i > ny - 2) ? mk(0, 0) : x; });
-  for (int j = 0; j <= ny; ++j) {
+  const cd* v = a.scrp;
+  int r0, r1;
+  row_range(g.ny + 1, blockIdx.y, gridDim.y, r0, r1);
+  for (int j = r0; j < r1; ++j) {
     const size_t o = (size_t)j * M + m;
     a.m2[o] = a.m2[o] + band_row(Ss2T, j, v, M, m) - k2 * band_row(Ss0T, j, v, M, m);
     a.rphi[o] = a.rphi[o] + (a.dt * a.al) * v[o];
@@ -397,18 +406,53 @@ __global__ void k_adj_eval_p1(Grid g, DBand B0gT, DBand B1gT, DBand B2gT, DBand 
   }
 }
 
-// transpose of k_mc_solve: (m1^c bar, m2^c bar, m3^c bar) -> rho_t bar
-__global__ void k_adj_mc(Grid g, DLU lu, DBand Bs1T, const double* dstar, const cd* m1b, const cd* m2b, const cd* m3b,
-                         cd* rtb, cd* scr) {
+// transpose of the m^c computation (k_mc_rhs, banded solve, k_mc_post): (m1^c, m2^c, m3^c) bar -> rho_t bar
+// Three launches: k_adj_mc_rhs (right-hand side of the transposed m2^c solve into scr),
+// the transposed banded solve (in place, per-mode factors, rows 0 and ny zero), k_adj_mc_post (rtbar).
+// q_i = conj(i / k) (k1/k m1bar_i + k3/k m3bar_i) is the adjoint of m_par_i.
+__device__ inline cd adj_mc_q(const cd* m1b, const cd* m3b, size_t o, double k1, double k3, double ik) {
+  const cd t = (k1 * ik) * m1b[o] + (k3 * ik) * m3b[o];
+  return ik * mk(t.im, -t.re);
+}
+
+// rows 0..ny split over gridDim.y chunks
+__global__ void k_adj_mc_rhs(Grid g, const double* dstar, const cd* m1b, const cd* m2b, const cd* m3b, cd* scr) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= (int)g.M) return;
   const size_t M = g.M;
   const int ny = g.ny;
+  int r0, r1;
+  row_range(ny + 1, blockIdx.y, gridDim.y, r0, r1);
+  if (m == 0 || is_nyquist(g, m)) {
+    for (int j = r0; j < r1; ++j) scr[(size_t)j * M + m] = mk(0, 0);
+    return;
+  }
+  double k1, k3;
+  wavenumbers(g, m, k1, k3);
+  const double ik = 1.0 / sqrt(k1 * k1 + k3 * k3);
+  for (int j = r0; j < r1; ++j) {
+    cd r = m2b[(size_t)j * M + m];
+    if (j >= 1) r = r + __ldg(dstar + j - 1) * adj_mc_q(m1b, m3b, (size_t)(j - 1) * M + m, k1, k3, ik);
+    if (j < ny) r = r - __ldg(dstar + j) * adj_mc_q(m1b, m3b, (size_t)j * M + m, k1, k3, ik);
+    scr[(size_t)j * M + m] = r;
+  }
+}
+
+// rows 0..ny-1 split over gridDim.y chunks; the k = 0 mode is one serial pass (chunk 0)
+__global__ void k_adj_mc_post(Grid g, DBand Bs1T, const double* dstar, const cd* m1b, const cd* m2b, const cd* m3b,
+                              const cd* scr, cd* rtb) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= (int)g.M) return;
+  const size_t M = g.M;
+  const int ny = g.ny;
+  int r0, r1;
+  row_range(ny, blockIdx.y, gridDim.y, r0, r1);
   if (is_nyquist(g, m)) {
-    for (int i = 0; i < ny; ++i) rtb[(size_t)i * M + m] = mk(0, 0);
+    for (int i = r0; i < r1; ++i) rtb[(size_t)i * M + m] = mk(0, 0);
     return;
   }
   if (m == 0) {  // m2c_i = sum_{j >= i, j < ny} rt_j / alpha_j
+    if (blockIdx.y != 0) return;
     cd s = mk(0, 0);
     for (int j = 0; j < ny; ++j) {
       s = s + m2b[(size_t)j * M];
@@ -418,22 +462,9 @@ __global__ void k_adj_mc(Grid g, DLU lu, DBand Bs1T, const double* dstar, const 
   }
   double k1, k3;
   wavenumbers(g, m, k1, k3);
-  const double k = sqrt(k1 * k1 + k3 * k3), ik = 1.0 / k;
-  // q_i = conj(i / k) * (k1/k m1bar_i + k3/k m3bar_i)
-  auto q = [&](int i) {
-    const cd t = (k1 * ik) * m1b[(size_t)i * M + m] + (k3 * ik) * m3b[(size_t)i * M + m];
-    return ik * mk(t.im, -t.re);
-  };
-  band_solve_T(
-      lu, m, scr, M,
-      [&](int j) {
-        cd r = m2b[(size_t)j * M + m];
-        if (j >= 1) r = r + __ldg(dstar + j - 1) * q(j - 1);
-        if (j < ny) r = r - __ldg(dstar + j) * q(j);
-        return r;
-      },
-      [&](int i, cd x, cd) { scr[(size_t)i * M + m] = (i == 0 || i == ny) ? mk(0, 0) : x; });
-  for (int i = 0; i < ny; ++i) rtb[(size_t)i * M + m] = q(i) - band_row(Bs1T, i, scr, M, m);
+  const double ik = 1.0 / sqrt(k1 * k1 + k3 * k3);
+  for (int i = r0; i < r1; ++i)
+    rtb[(size_t)i * M + m] = adj_mc_q(m1b, m3b, (size_t)i * M + m, k1, k3, ik) - band_row(Bs1T, i, scr, M, m);
 }
 
 // BDF guess adjoint: zbar += a0/dt zdbar, zh_k bar += a_{k+1}/dt zdbar
@@ -595,11 +626,21 @@ void f_transpose(Ctx& c, cd* const* spec, double* const* phys, int nf) {  // ove
   wscale(c, spec, nf, 1.0 / pp, 0.5 / pp);
   fft_inverse_as(c, spec, phys, nf, 0);
 }
+// out = A^{-T} in per job (one launch), boundary rows outside [zlo, zhi] zero
+void solve_T_jobs(Ctx& c, KClass cls, const DLU& lu, std::initializer_list<SolveTJob> jobs) {
+  SolveTJobs sj{};
+  int n = 0;
+  for (const SolveTJob& j : jobs) sj.j[n++] = j;
+  const double rowsM = (double)lu.n * c.g.M;
+  const int tpm = solve_split(c.g);
+  const dim3 grid((unsigned)((tpm * c.g.M + TPB - 1) / TPB), n);
+  if (tpm == 2)
+    LMVD_LAUNCH(c, cls, n * lu.flops_per_mode * c.g.M, 32.0 * rowsM * n, k_solve_T_re, grid, TPB, 0, c.g, lu, sj);
+  else
+    LMVD_LAUNCH(c, cls, n * lu.flops_per_mode * c.g.M, 32.0 * rowsM * n, k_solve_T_cd, grid, TPB, 0, c.g, lu, sj);
+}
 void solve_T(Ctx& c, const DLU& lu, const cd* in, cd* out) {
-  SolveJobs sj{};
-  sj.j[0] = SolveJob{in, nullptr, out};
-  LMVD_LAUNCH(c, KC_SOLVE, lu.flops_per_mode * c.g.M, 32.0 * lu.n * c.g.M, k_solve_shared_T, dim3(mblocks(c.g), 1), TPB,
-              0, c.g, lu, sj);
+  solve_T_jobs(c, KC_SOLVE, lu, {SolveTJob{in, out, 0, lu.n - 1}});
 }
 void eval_T(Ctx& c, std::initializer_list<EvalJob> jobs) {
   EvalJobs ej{};
@@ -618,8 +659,12 @@ void chain_mc_T(Ctx& c, AdjWork& A, double* const* bb, const double* a_tape, int
   g_transpose(c, bb, sv3, 3);
   eval_T(c, {EvalJob{A.B0gT, A.sv[0], A.mc[0], 0}, EvalJob{A.Sg0T, A.sv[1], A.mc[1], 0},
              EvalJob{A.B0gT, A.sv[2], A.mc[2], 0}});
-  LMVD_LAUNCH(c, KC_MC_SOLVE, 0, 0, k_adj_mc, mblocks(c.g), TPB, 0, c.g, c.lu_mc, A.BsT[1], c.dstar, A.mc[0],
-              A.mc[1], A.mc[2], A.rt, A.tSp);
+  const int ny = c.g.ny;
+  LMVD_LAUNCH(c, KC_MC_SOLVE, 0, 0, k_adj_mc_rhs, dim3(mblocks(c.g), row_chunks(c.g, ny + 1)), TPB, 0, c.g, c.dstar,
+              A.mc[0], A.mc[1], A.mc[2], A.tSp);
+  solve_T_jobs(c, KC_MC_SOLVE, c.lu_mc, {SolveTJob{A.tSp, A.tSp, 1, ny - 1}});
+  LMVD_LAUNCH(c, KC_MC_SOLVE, 0, 0, k_adj_mc_post, dim3(mblocks(c.g), row_chunks(c.g, ny)), TPB, 0, c.g, A.BsT[1],
+              c.dstar, A.mc[0], A.mc[1], A.mc[2], A.tSp, A.rt);
   solve_T(c, c.lu_interp, A.rt, A.tS);
   cd* t1[1] = {A.tS};
   double* rtp[1] = {A.pb[3]};
@@ -677,20 +722,23 @@ int adjoint_impl(Ctx& c) {
   u.om = A.om; u.rom = A.rom; u.romp = A.romp; u.z = A.z; u.zd = A.zd; u.zdp = A.zdp;
   u.m2 = A.m2; u.rphi = A.rphi; u.rphip = A.rphip; u.mm1 = A.mm1; u.mm3 = A.mm3; u.rm = A.rm; u.rmp = A.rmp;
   u.scr0 = A.tS; u.scr1 = A.tS + S; u.scrp = A.tSp;
-  LMVD_LAUNCH(c, KC_UPDATE, 0, 0, k_adj_update_om_z, dim3(mblocks(g), 2), TPB, 0, g, A.B0gT, c.lu_interp,
-              c.lu_neumann, u);
+  solve_T_jobs(c, KC_UPDATE, c.lu_interp, {SolveTJob{A.oom, u.scr0, 1, ny - 2}});
+  solve_T_jobs(c, KC_UPDATE, c.lu_neumann, {SolveTJob{A.oz, u.scr1, 1, ny - 2}});
+  LMVD_LAUNCH(c, KC_UPDATE, 0, 0, k_adj_update_om_z_post, dim3(mblocks(g), row_chunks(g, ny), 2), TPB, 0, g, A.B0gT,
+              u);
   LMVD_LAUNCH(c, KC_UPDATE, 0, 0, k_adj_update_means, 1, 32, 0, g, A.B0gT, c.lu_means, u);
-  LMVD_LAUNCH(c, KC_UPDATE, 0, 0, k_adj_update_m2, mblocks(g), TPB, 0, g, A.Ss0T, A.Ss2T, c.lu_md, u);
+  solve_T_jobs(c, KC_UPDATE, c.lu_md, {SolveTJob{A.om2, u.scrp, 2, ny - 2}});
+  LMVD_LAUNCH(c, KC_UPDATE, 0, 0, k_adj_update_m2_post, dim3(mblocks(g), row_chunks(g, ny + 1)), TPB, 0, g, A.Ss0T,
+              A.Ss2T, u);
   // step 5: RHS streams, collocation solves, transforms, products of pass 2
   St7 stw{};
   for (int q = 0; q < 7; ++q) stw.p[q] = A.st[q];
   LMVD_LAUNCH(c, KC_RHS_EVAL, 0, 0, k_adj_rhs_eval, mblocks(g), TPB, 0, g, A.B1gT, A.B2gT, A.BsT[0], A.BsT[1],
               A.BsT[2], A.BsT[3], A.rom, A.rphi, A.rm, stw);
-  {
-    SolveJobs sj{};
-    for (int q = 1; q <= 6; ++q) sj.j[q - 1] = SolveJob{A.st[q], nullptr, A.st[q]};
-    LMVD_LAUNCH(c, KC_SOLVE, 0, 0, k_solve_shared_T, dim3(mblocks(g), 6), TPB, 0, g, c.lu_interp, sj);
-  }
+  solve_T_jobs(c, KC_SOLVE, c.lu_interp,
+               {SolveTJob{A.st[1], A.st[1], 0, ny - 1}, SolveTJob{A.st[2], A.st[2], 0, ny - 1},
+                SolveTJob{A.st[3], A.st[3], 0, ny - 1}, SolveTJob{A.st[4], A.st[4], 0, ny - 1},
+                SolveTJob{A.st[5], A.st[5], 0, ny - 1}, SolveTJob{A.st[6], A.st[6], 0, ny - 1}});
   FieldsW10 svw{};
   for (int q = 0; q < 10; ++q) svw.p[q] = A.sv[q];
   LMVD_LAUNCH(c, KC_RHS_COMBINE, 0, 0, k_adj_rhs_combine, eblocks(S), 256, 0, g, 1.0 / cf.re, 1.0 / (cf.fr * cf.fr),

@@ -303,7 +303,9 @@ void eval_jobs(Ctx& c, std::initializer_list<EvalJob> jobs) {
               dim3(mode_blocks(c.g), n, row_chunks(c.g, maxrows)), TPB_MODE, 0, c.g, ej);
 }
 
-void solve_interp(Ctx& c, std::initializer_list<SolveJob> jobs, const DLU& lu) {
+// out = A^{-1} in (+ add) for each job; shared or per-mode factors; one or two threads per mode
+// (solve_split)
+void solve_modes(Ctx& c, KClass cls, std::initializer_list<SolveJob> jobs, const DLU& lu) {
   SolveJobs sj{};
   int n = 0;
   double arrays = 0;
@@ -312,9 +314,17 @@ void solve_interp(Ctx& c, std::initializer_list<SolveJob> jobs, const DLU& lu) {
     arrays += j.add ? 3 : 2;
   }
   const double rowsM = (double)lu.n * c.g.M;
-  LMVD_LAUNCH(c, KC_SOLVE, n * lu.flops_per_mode * c.g.M, 16.0 * arrays * rowsM, k_solve_shared,
-              dim3(mode_blocks(c.g), n), TPB_MODE, 0, c.g, lu, sj);
+  const double factors = lu.mstride ? 8.0 * (2 * lu.K + 1) * rowsM * n : 0.0;
+  const int tpm = solve_split(c.g);
+  const unsigned blocks = (unsigned)((tpm * c.g.M + TPB_MODE - 1) / TPB_MODE);
+  if (tpm == 2)
+    LMVD_LAUNCH(c, cls, n * lu.flops_per_mode * c.g.M, 16.0 * arrays * rowsM + factors, k_solve_re, dim3(blocks, n),
+                TPB_MODE, 0, c.g, lu, sj);
+  else
+    LMVD_LAUNCH(c, cls, n * lu.flops_per_mode * c.g.M, 16.0 * arrays * rowsM + factors, k_solve_cd, dim3(blocks, n),
+                TPB_MODE, 0, c.g, lu, sj);
 }
+void solve_interp(Ctx& c, std::initializer_list<SolveJob> jobs, const DLU& lu) { solve_modes(c, KC_SOLVE, jobs, lu); }
 
 // steps 1-2: m^d and z-derived fields in physical space; rho, 1/rho, f', grad z / rho; R_z.
 // zp: where z, dz/dx, dz/dz, dz/dy, lap z land on the physical grid (work fields by default; the adjoint
@@ -376,9 +386,12 @@ void mc_from_zdot(Ctx& c, double* a = nullptr, double* const* b = nullptr) {
   solve_interp(c, {SolveJob{c.sv[1], nullptr, c.rt}}, c.lu_interp);
   {
     const double rowsM = (double)(c.g.ny + 1) * c.g.M;
-    LMVD_LAUNCH(c, KC_MC_SOLVE, c.lu_mc.flops_per_mode * c.g.M + rowsM * (4.0 * c.Bs[1].w + 20.0),
-                rowsM * (16.0 * 4 + 8.0 * (2 * c.lu_mc.K + 1)), k_mc_solve, mode_blocks(c.g), TPB_MODE, 0, c.g,
-                c.lu_mc, c.Bs[1], c.dstar, c.rt, c.m1c, c.m2c, c.m3c);
+    LMVD_LAUNCH(c, KC_MC_SOLVE, rowsM * 4.0 * c.Bs[1].w, rowsM * 16.0 * 2, k_mc_rhs,
+                dim3(mode_blocks(c.g), row_chunks(c.g, c.g.ny + 1)), TPB_MODE, 0, c.g, c.Bs[1], c.rt, c.m2c);
+    solve_modes(c, KC_MC_SOLVE, {SolveJob{c.m2c, nullptr, c.m2c}}, c.lu_mc);
+    LMVD_LAUNCH(c, KC_MC_SOLVE, rowsM * 20.0, rowsM * 16.0 * 5, k_mc_post,
+                dim3(mode_blocks(c.g), row_chunks(c.g, c.g.ny)), TPB_MODE, 0, c.g, c.dstar, c.rt, c.m1c, c.m2c,
+                c.m3c);
   }
   eval_jobs(c, {EvalJob{c.B0g, c.m1c, c.sv[0], 0}, EvalJob{c.Sg0, c.m2c, c.sv[1], 0}, EvalJob{c.B0g, c.m3c, c.sv[2], 0}});
   cd* in[3] = {c.sv[0], c.sv[1], c.sv[2]};
@@ -486,15 +499,16 @@ int advance_impl(Ctx& c, const Tape* tape) {
   u.m2 = c.m2; u.r_phi = c.r_phi; u.r_phi_prev = c.r_phi_prev;
   u.mm1 = c.mm1; u.mm3 = c.mm3; u.r_m = c.r_m; u.r_m_prev = c.r_m_prev;
   u.om_new = c.om_new; u.z_new = c.z_new; u.m2_new = c.m2_new; u.mm1_new = c.mm1_new; u.mm3_new = c.mm3_new;
-  LMVD_LAUNCH(c, KC_UPDATE, (c.lu_interp.flops_per_mode + c.lu_neumann.flops_per_mode) * g.M + S * (12.0 * c.B0g.w + 20.0),
-              16.0 * 8 * S, k_update_om_z,
-              dim3(mode_blocks(g), 2), TPB_MODE, 0, g, c.B0g, c.lu_interp, c.lu_neumann, u);
+  LMVD_LAUNCH(c, KC_UPDATE, S * (12.0 * c.B0g.w + 20.0), 16.0 * 7 * S, k_update_om_z_rhs,
+              dim3(mode_blocks(g), row_chunks(g, g.ny), 2), TPB_MODE, 0, g, c.B0g, u);
+  solve_modes(c, KC_UPDATE, {SolveJob{c.om_new, nullptr, c.om_new}}, c.lu_interp);
+  solve_modes(c, KC_UPDATE, {SolveJob{c.z_new, nullptr, c.z_new}}, c.lu_neumann);
   LMVD_LAUNCH(c, KC_UPDATE, 0, 0, k_update_means, 1, 32, 0, g, c.B0g, c.lu_means, u);
   {
     const double Sp = (double)(g.ny + 1) * g.M;
-    LMVD_LAUNCH(c, KC_UPDATE, c.lu_md.flops_per_mode * g.M + Sp * (8.0 * c.Ss0.w + 10.0),
-                Sp * (16.0 * 4 + 8.0 * (2 * c.lu_md.K + 1)), k_update_m2, mode_blocks(g), TPB_MODE, 0, g, c.Ss0,
-                c.Ss2, c.lu_md, u);
+    LMVD_LAUNCH(c, KC_UPDATE, Sp * (8.0 * c.Ss0.w + 10.0), 16.0 * 4 * Sp, k_update_m2_rhs,
+                dim3(mode_blocks(g), row_chunks(g, g.ny + 1)), TPB_MODE, 0, g, c.Ss0, c.Ss2, u);
+    solve_modes(c, KC_UPDATE, {SolveJob{c.m2_new, nullptr, c.m2_new}}, c.lu_md);
   }
   // history rotation (pointer swaps)
   cd* oldest = c.zh[2];

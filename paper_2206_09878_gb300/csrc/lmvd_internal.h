@@ -81,6 +81,10 @@ inline unsigned row_chunks(const Grid& g, int rows) {
   return (unsigned)(ch > 1 ? ch : 1);
 }
 
+// Threads per mode of the banded-solve kernels: 2 (one per real part) when the grid has fewer than 65536
+// Fourier modes per row, else 1 (see band_solve_v).
+inline int solve_split(const Grid& g) { return g.M < 65536 ? 2 : 1; }
+
 __device__ inline cd band_row(const DBand& B, int i, const cd* x, size_t M, int m) {
   const int c = B.c0[i];
   const double* v = B.v + (size_t)i * B.w;
@@ -146,8 +150,6 @@ struct Ctx {
   double* dstar = nullptr;  // ny entries: (D* c)_i = dstar[i] (c_{i+1} - c_i)
   DLU lu_interp, lu_neumann, lu_mc, lu_md;
   DLU lu_means;  // lu_interp (walls) or lu_neumann (potential matching): not owned
-  double* A2mc = nullptr; double* A0mc = nullptr; double* A2md = nullptr; double* A0md = nullptr;
-  int Kmc = 0, Kmd = 0;
   FFTPlan fx, fz;
 
   // memory arena

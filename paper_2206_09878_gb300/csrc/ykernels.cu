@@ -75,43 +75,70 @@ __global__ void k_eval(Grid g, EvalJobs jobs) {
     jb.out[(size_t)i * M + m] = ny ? mk(0, 0) : band_row(jb.B, i, jb.in, M, m);
 }
 
-// ------------------------------------------------------------------ shared-factor solves
-// field blockIdx.y: out = A^{-1} in (+ add); used for collocation (interpolation) solves.
-__global__ void k_solve_shared(Grid g, DLU lu, SolveJobs jobs) {
-  const int m = blockIdx.x * blockDim.x + threadIdx.x;
-  if (m >= (int)g.M) return;
-  const SolveJob& jb = jobs.j[blockIdx.y];
+// ------------------------------------------------------------------ banded solves
+// job blockIdx.y: out = A^{-1} in (+ add), factors shared or per mode (DLU.mstride); used for the
+// collocation (interpolation) solves and the per-mode systems. out may alias in. Nyquist modes are set to
+// zero. k_solve_cd: one thread per mode; k_solve_re: one thread per (mode, real part), see band_solve_v.
+template <class V>
+__device__ void solve_job(const Grid& g, const DLU& lu, const SolveJob& jb) {
+  constexpr int TPM = sizeof(V) == sizeof(cd) ? 1 : 2;
+  const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (t >= TPM * g.M) return;
+  const int m = (int)(t / TPM), comp = (int)(t % TPM);
   const size_t M = g.M;
+  V* out = reinterpret_cast<V*>(jb.out);
   if (is_nyquist(g, m)) {
-    for (int i = 0; i < lu.n; ++i) jb.out[(size_t)i * M + m] = mk(0, 0);
+    for (int i = 0; i < lu.n; ++i) out[vidx<V>(i, M, m, comp)] = vzero<V>();
     return;
   }
-  const cd* in = jb.in;
-  const cd* add = jb.add;
-  cd* out = jb.out;
-  band_solve(
-      lu, m, out, M, [&](int i) { return in[(size_t)i * M + m]; },
-      [&](int i, cd x, cd) { out[(size_t)i * M + m] = add ? x + add[(size_t)i * M + m] : x; });
+  band_solve_v<V>(lu, m, comp, reinterpret_cast<const V*>(jb.in), reinterpret_cast<const V*>(jb.add), out, M);
 }
+__global__ void k_solve_cd(Grid g, DLU lu, SolveJobs jobs) { solve_job<cd>(g, lu, jobs.j[blockIdx.y]); }
+__global__ void k_solve_re(Grid g, DLU lu, SolveJobs jobs) { solve_job<double>(g, lu, jobs.j[blockIdx.y]); }
 
 // ------------------------------------------------------------------ m^c from rho_t
 // Eq. COM_fourier + CF_fourier with m_par eliminated: rows 1..ny-1 collocate
-// (B*'' - k^2 B*) m2^c = -B' rho_t at the interior order-(p+1) Greville points, rows 0 and ny set
-// m2^c(+-1) = 0 (walls). Then m_par = i (rho_t + D* m2^c) / k (exact mass conservation in
-// B-coefficient space) and Eq. mc_recon m1^c = k1/k m_par, m3^c = k3/k m_par.
+// (B*'' - k^2 B*) m2^c = -B' rho_t at the interior order-(p+1) Greville points, rows 0 and ny hold the
+// boundary rows (walls: m2^c(+-1) = 0; potential matching: the Robin rows), all with zero right-hand side.
+// Then m_par = i (rho_t + D* m2^c) / k (exact mass conservation in B-coefficient space) and
+// Eq. mc_recon m1^c = k1/k m_par, m3^c = k3/k m_par.
 // k = 0 (Eq. mc_mean): D* <m2^c> = -<rho_t> with <m2^c>(+1) = 0; <m1^c> = <m3^c> = 0.
-__global__ void k_mc_solve(Grid g, DLU lu, DBand Bs1, const double* dstar, const cd* rt, cd* m1c, cd* m2c,
-                           cd* m3c) {
+// Three launches: k_mc_rhs (right-hand side into m2c), the banded solve (in place, per-mode factors),
+// k_mc_post (m1c, m3c; the k = 0 mean).
+
+// rows 0..ny split over gridDim.y chunks
+__global__ void k_mc_rhs(Grid g, DBand Bs1, const cd* rt, cd* m2c) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= (int)g.M) return;
   const size_t M = g.M;
   const int ny = g.ny;
+  int r0, r1;
+  row_range(ny + 1, blockIdx.y, gridDim.y, r0, r1);
+  const bool zero = m == 0 || is_nyquist(g, m);
+  for (int i = r0; i < r1; ++i) {
+    cd v = mk(0, 0);
+    if (!zero && i > 0 && i < ny) {
+      const cd d = band_row(Bs1, i, rt, M, m);
+      v = mk(-d.re, -d.im);
+    }
+    m2c[(size_t)i * M + m] = v;
+  }
+}
+
+// rows 0..ny-1 split over gridDim.y chunks; the k = 0 mode is one serial pass (chunk 0)
+__global__ void k_mc_post(Grid g, const double* dstar, const cd* rt, cd* m1c, cd* m2c, cd* m3c) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= (int)g.M) return;
+  const size_t M = g.M;
+  const int ny = g.ny;
+  int r0, r1;
+  row_range(ny, blockIdx.y, gridDim.y, r0, r1);
   if (is_nyquist(g, m)) {
-    for (int i = 0; i <= ny; ++i) m2c[(size_t)i * M + m] = mk(0, 0);
-    for (int i = 0; i < ny; ++i) m1c[(size_t)i * M + m] = m3c[(size_t)i * M + m] = mk(0, 0);
+    for (int i = r0; i < r1; ++i) m1c[(size_t)i * M + m] = m3c[(size_t)i * M + m] = mk(0, 0);
     return;
   }
   if (m == 0) {
+    if (blockIdx.y != 0) return;
     cd c = mk(0, 0);
     m2c[(size_t)ny * M] = c;
     for (int i = ny - 1; i >= 0; --i) {
@@ -124,22 +151,13 @@ __global__ void k_mc_solve(Grid g, DLU lu, DBand Bs1, const double* dstar, const
   double k1, k3;
   wavenumbers(g, m, k1, k3);
   const double k = sqrt(k1 * k1 + k3 * k3), ik = 1.0 / k;
-  band_solve(
-      lu, m, m2c, M,
-      [&](int i) {
-        if (i == 0 || i == ny) return mk(0, 0);
-        const cd d = band_row(Bs1, i, rt, M, m);
-        return mk(-d.re, -d.im);
-      },
-      [&](int i, cd x, cd xnext) {
-        m2c[(size_t)i * M + m] = x;
-        if (i < ny) {
-          const cd dm = __ldg(dstar + i) * (xnext - x);
-          const cd mpar = ik * times_i(rt[(size_t)i * M + m] + dm);
-          m1c[(size_t)i * M + m] = (k1 * ik) * mpar;
-          m3c[(size_t)i * M + m] = (k3 * ik) * mpar;
-        }
-      });
+  for (int i = r0; i < r1; ++i) {
+    const cd x = m2c[(size_t)i * M + m], xn = m2c[(size_t)(i + 1) * M + m];
+    const cd dm = __ldg(dstar + i) * (xn - x);
+    const cd mpar = ik * times_i(rt[(size_t)i * M + m] + dm);
+    m1c[(size_t)i * M + m] = (k1 * ik) * mpar;
+    m3c[(size_t)i * M + m] = (k3 * ik) * mpar;
+  }
 }
 
 // ------------------------------------------------------------------ RHS streams (Eq. DNS_system)
@@ -218,45 +236,38 @@ __global__ void k_rhs_eval(Grid g, DBand B1g, DBand B2g, DBand Bs0, DBand Bs1, D
 
 // ------------------------------------------------------------------ RK2 update (step 6)
 // Midpoint RK2 in low-storage form at the collocation points, X^{s+1} = X^s + dt (al R^s + be R^{s-1}),
-// followed by the wall-row solves. Omega2 (job 0): values at g, Dirichlet rows (interpolation LU);
-// z (job 1): values at g advanced with (dz/dt)^{k_f}, Neumann rows dz/dy(+-1) = 0 (Neumann LU).
-__global__ void k_update_om_z(Grid g, DBand B0g, DLU lu_i, DLU lu_n, UpdateArgs a) {
+// followed by the boundary-row solves (banded solves in place). Omega2 (blockIdx.z = 0): values at g,
+// Dirichlet rows (interpolation LU); z (blockIdx.z = 1): values at g advanced with (dz/dt)^{k_f},
+// Neumann rows dz/dy(+-1) = 0 (Neumann LU). This kernel writes the right-hand sides; rows split over
+// gridDim.y chunks.
+__global__ void k_update_om_z_rhs(Grid g, DBand B0g, UpdateArgs a) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= (int)g.M) return;
   const size_t M = g.M;
   const int ny = g.ny;
-  const int job = blockIdx.y;
+  const int job = blockIdx.z;
   cd* out = job == 0 ? a.om_new : a.z_new;
-  if (is_nyquist(g, m) || (job == 0 && m == 0)) {
-    for (int i = 0; i < ny; ++i) out[(size_t)i * M + m] = mk(0, 0);
-    return;
-  }
+  int r0, r1;
+  row_range(ny, blockIdx.y, gridDim.y, r0, r1);
+  const bool zero = is_nyquist(g, m) || (job == 0 && m == 0);
   const double dt = a.dt, al = a.al, be = a.be;
-  if (job == 0) {
-    band_solve(
-        lu_i, m, out, M,
-        [&](int i) {
-          if (i == 0 || i == ny - 1) return mk(0, 0);
-          const size_t o = (size_t)i * M + m;
-          return band_row(B0g, i, a.om, M, m) + dt * (al * a.r_om[o] + be * a.r_om_prev[o]);
-        },
-        [&](int i, cd x, cd) { out[(size_t)i * M + m] = x; });
-  } else {
-    band_solve(
-        lu_n, m, out, M,
-        [&](int i) {
-          if (i == 0 || i == ny - 1) return mk(0, 0);
-          const int c = B0g.c0[i];
-          const double* v = B0g.v + (size_t)i * B0g.w;
-          cd acc = mk(0, 0);
-          for (int q = 0; q < B0g.w; ++q) {
-            const size_t o = (size_t)(c + q) * M + m;
-            const cd zz = a.z[o] + dt * (al * a.zdot[o] + be * a.zdot_prev[o]);
-            acc = fma_rc(__ldg(v + q), zz, acc);
-          }
-          return acc;
-        },
-        [&](int i, cd x, cd) { out[(size_t)i * M + m] = x; });
+  for (int i = r0; i < r1; ++i) {
+    cd v = mk(0, 0);
+    if (!zero && i > 0 && i < ny - 1) {
+      if (job == 0) {
+        const size_t o = (size_t)i * M + m;
+        v = band_row(B0g, i, a.om, M, m) + dt * (al * a.r_om[o] + be * a.r_om_prev[o]);
+      } else {
+        const int c = B0g.c0[i];
+        const double* w = B0g.v + (size_t)i * B0g.w;
+        for (int q = 0; q < B0g.w; ++q) {
+          const size_t o = (size_t)(c + q) * M + m;
+          const cd zz = a.z[o] + dt * (al * a.zdot[o] + be * a.zdot_prev[o]);
+          v = fma_rc(__ldg(w + q), zz, v);
+        }
+      }
+    }
+    out[(size_t)i * M + m] = v;
   }
 }
 
@@ -293,31 +304,32 @@ __global__ void k_update_means(Grid g, DBand B0g, DLU lu_i, UpdateArgs a) {
   }
 }
 
-// m2^d (Eq. phi_poisson): phi2 = (B*'' - k^2 B*) m2^d at g*_2 .. g*_{ny-2} advanced with RHS_phi2,
-// four no-slip rows m2^d(+-1) = dm2^d/dy(+-1) = 0; per-mode LU. k = 0: m2^d = 0.
-__global__ void k_update_m2(Grid g, DBand Ss0, DBand Ss2, DLU lu, UpdateArgs a) {
+// m2^d (Eq. phi_poisson): phi2 = (B*'' - k^2 B*) m2^d at g*_2 .. g*_{ny-2} advanced with RHS_phi2, four
+// boundary rows (no-slip or potential matching) with zero right-hand side; k = 0: m2^d = 0. This kernel
+// writes the right-hand side into m2_new (rows split over gridDim.y chunks); the banded solve with the
+// per-mode factors then runs in place.
+__global__ void k_update_m2_rhs(Grid g, DBand Ss0, DBand Ss2, UpdateArgs a) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= (int)g.M) return;
   const size_t M = g.M;
   const int ny = g.ny;
+  int r0, r1;
+  row_range(ny + 1, blockIdx.y, gridDim.y, r0, r1);
   cd* out = a.m2_new;
-  if (m == 0 || is_nyquist(g, m)) {
-    for (int i = 0; i <= ny; ++i) out[(size_t)i * M + m] = mk(0, 0);
-    return;
-  }
-  double k1, k3;
-  wavenumbers(g, m, k1, k3);
+  const bool zero = m == 0 || is_nyquist(g, m);
+  double k1 = 0.0, k3 = 0.0;
+  if (!zero) wavenumbers(g, m, k1, k3);
   const double k2 = k1 * k1 + k3 * k3;
   const double dt = a.dt, al = a.al, be = a.be;
-  band_solve(
-      lu, m, out, M,
-      [&](int i) {
-        if (i < 2 || i > ny - 2) return mk(0, 0);
-        const size_t o = (size_t)i * M + m;
-        const cd phi = band_row(Ss2, i, a.m2, M, m) - k2 * band_row(Ss0, i, a.m2, M, m);
-        return phi + dt * (al * a.r_phi[o] + be * a.r_phi_prev[o]);
-      },
-      [&](int i, cd x, cd) { out[(size_t)i * M + m] = x; });
+  for (int i = r0; i < r1; ++i) {
+    cd v = mk(0, 0);
+    if (!zero && i >= 2 && i <= ny - 2) {
+      const size_t o = (size_t)i * M + m;
+      const cd phi = band_row(Ss2, i, a.m2, M, m) - k2 * band_row(Ss0, i, a.m2, M, m);
+      v = phi + dt * (al * a.r_phi[o] + be * a.r_phi_prev[o]);
+    }
+    out[(size_t)i * M + m] = v;
+  }
 }
 
 // ------------------------------------------------------------------ elementwise helpers

@@ -44,15 +44,16 @@ struct UpdateArgs {
 __global__ void k_eval_p1(Grid g, DBand B0g, DBand B1g, DBand B2g, DBand Sg0, DBand Sg1, const cd* z,
                           const cd* om, const cd* m2, const double* mm1, const double* mm3, Fields8 out);
 __global__ void k_eval(Grid g, EvalJobs jobs);
-__global__ void k_solve_shared(Grid g, DLU lu, SolveJobs jobs);
-__global__ void k_mc_solve(Grid g, DLU lu, DBand Bs1, const double* dstar, const cd* rt, cd* m1c, cd* m2c,
-                           cd* m3c);
+__global__ void k_solve_cd(Grid g, DLU lu, SolveJobs jobs);
+__global__ void k_solve_re(Grid g, DLU lu, SolveJobs jobs);
+__global__ void k_mc_rhs(Grid g, DBand Bs1, const cd* rt, cd* m2c);
+__global__ void k_mc_post(Grid g, const double* dstar, const cd* rt, cd* m1c, cd* m2c, cd* m3c);
 __global__ void k_rhs_combine(Grid g, double mu, double grav, Fields10C sv, Fields7 st);
 __global__ void k_rhs_eval(Grid g, DBand B1g, DBand B2g, DBand Bs0, DBand Bs1, DBand Bs2, DBand Bs3, Fields7C st,
                            cd* r_om, cd* r_phi, double* r_m);
-__global__ void k_update_om_z(Grid g, DBand B0g, DLU lu_i, DLU lu_n, UpdateArgs a);
+__global__ void k_update_om_z_rhs(Grid g, DBand B0g, UpdateArgs a);
 __global__ void k_update_means(Grid g, DBand B0g, DLU lu_i, UpdateArgs a);
-__global__ void k_update_m2(Grid g, DBand Ss0, DBand Ss2, DLU lu, UpdateArgs a);
+__global__ void k_update_m2_rhs(Grid g, DBand Ss0, DBand Ss2, UpdateArgs a);
 __global__ void k_bdf(size_t n, double a0, double a1, double a2, double a3, double idt, const cd* z, const cd* h0,
                       const cd* h1, const cd* h2, cd* out);
 __global__ void k_backfill(size_t n, double c0, double c1, double c2, const cd* z, const cd* zdot, cd* h0, cd* h1,

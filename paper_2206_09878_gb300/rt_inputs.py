@@ -48,6 +48,9 @@ WORKLOADS = {
                   re=5000.0, dt=1e-4, steps=10, seed=1003),
     "rt768": dict(nx=768, ny=769, nz=768, ratio=25.7, width=0.02, kmax=48, eta_rms=1e-3, u_rms=1e-4,
                   re=8000.0, dt=2e-4 * 256 / 768, steps=5, seed=1005),
+    # rt512 with 33 B-spline rows: the same transform lengths (768) for a small ncu capture
+    "rt512y33": dict(nx=512, ny=33, nz=512, ratio=10.0, width=0.05, kmax=32, eta_rms=2e-3, u_rms=1e-4,
+                     re=5000.0, dt=1e-4, steps=1, seed=1003),
 }
 
 
