@@ -38,9 +38,13 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # df64.h (TwoSum-renormalised adds, FMA TwoProd products), i.e. 10 instructions per classic flop;
 # the FP32 pipe issues 152 SMs x 128 lanes x 2.07 GHz instructions per second.
 DF64_EQ_PEAK_TFLOPS = 152 * 128 * 2.07e9 / 10 / 1e12
-# DRAM bytes per launch of the dominant kernel from one ncu capture, by precision (None until captured
-# for the current code of that kernel)
-NCU_TRAFFIC_PER_LAUNCH = {0: None, 1: None}
+# DRAM bytes (read + write) per unit of the dominant kernel from one ncu capture of a smaller case with the
+# same transform length, keyed by (precision, kernel class, transform length); a unit of the x-passes is one
+# complex transform (a pair of real rows). Full launches are scaled by the units they process.
+#   (0, fft_x_inverse, 768): 2025.8 MB over 101376 units (512 x 33 x 512, 8 fields) = 19983 B per unit,
+#   (1, fft_x_inverse, 768): 2031.4 MB over the same units = 20038 B per unit,
+#   against 2 (16 nx/2 + 8 px) = 20480 algorithmic bytes.
+NCU_DRAM_BYTES_PER_UNIT = {(0, "fft_x_inverse", 768): 19983.0, (1, "fft_x_inverse", 768): 20038.0}
 CPU_SAMPLE_N = 128
 
 
@@ -264,7 +268,18 @@ def time_variant(L, w, precision, args, stream, st_host, local, ws, e2e_steps=0)
     return res, final
 
 
-def roofline_of(prof, ms_step_total, fp):
+def traffic_per_launch(fp, kernel, grid, alg_bytes_per_launch):
+    """DRAM bytes per launch from the ncu per-unit figure (None where no capture matches)."""
+    nx, _, nz = grid
+    px = 3 * nx // 2
+    per_unit = NCU_DRAM_BYTES_PER_UNIT.get((fp, kernel, px))
+    if per_unit is None or not kernel.startswith("fft_x") or not alg_bytes_per_launch:
+        return None
+    units = alg_bytes_per_launch / (2.0 * (16 * (nx // 2) + 8 * px))
+    return per_unit * units
+
+
+def roofline_of(prof, ms_step_total, fp, grid):
     """Dominant kernel class and its achieved algorithmic rate against the ALU peak of its arithmetic."""
     top = max(prof, key=lambda k: prof[k][0])
     tms, tn, tfl, tby = prof[top]
@@ -275,7 +290,10 @@ def roofline_of(prof, ms_step_total, fp):
         peak, note = DF64_EQ_PEAK_TFLOPS, ("FP64-equivalent peak of double-float on the FP32 pipe: 152 SMs x 128 "
                                             "lanes x 2.07 GHz / 10 FP32 instructions per classic flop")
     return {"kernel": top, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak if achieved else None, "traffic": NCU_TRAFFIC_PER_LAUNCH.get(fp),
+            "frac": achieved / peak if achieved else None,
+            "traffic": traffic_per_launch(fp, top, grid, tby / tn if tn else None),
+            "traffic_note": "ncu dram__bytes_read.sum + dram__bytes_write.sum per unit on 512x33x512 (same "
+                            "768-point transforms), scaled by the units of the average launch",
             "launches": int(tn), "algorithmic_bytes_per_launch": tby / tn if tn else None,
             "achieved_hbm_gbs": tby / (tms / 1e3) / 1e9 if tms > 0 else None, "peak_note": note,
             "share_of_step": tms / ms_step_total if ms_step_total > 0 else None}
@@ -425,7 +443,8 @@ def run_cuda(args):
         "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic (seeded Rayleigh-Taylor-shaped state)", "config": config,
         "clocks": res["clocks"], "gpu_launches": int(res["launches"]),
-        "roofline": roofline_of(prof, res["ms"], args.precision), "e2e": e2e, "kernels": breakdown,
+        "roofline": roofline_of(prof, res["ms"], args.precision, (w["nx"], w["ny"], w["nz"])), "e2e": e2e,
+        "kernels": breakdown,
     }
     if not args.no_variant:
         other = 1 - args.precision
@@ -437,7 +456,7 @@ def run_cuda(args):
                           "FP32-FFT: double-float (2 x FP32, error-free transformations) transforms and products, "
                           "FP64 solves / RHS / update"),
             "value": v2, "unit": UNIT, "ms_per_step": r2["ms"] / args.steps, "clocks": r2["clocks"],
-            "roofline": roofline_of(r2["prof"], r2["ms"], other),
+            "roofline": roofline_of(r2["prof"], r2["ms"], other, (w["nx"], w["ny"], w["nz"])),
             "kernels": {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps,
                             "tflops": (v[2] / (v[0] / 1e3) / 1e12) if v[0] > 0 else None}
                         for k, v in r2["prof"].items() if v[1] > 0},
