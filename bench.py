@@ -217,7 +217,9 @@ def time_variant(L, w, precision, args, stream, st_host, local, ws, e2e_steps=0)
     cfg = L.lmvd_default_config(w["nx"], w["ny"], w["nz"], re=w["re"], rho_light=1.0 / w["ratio"], dt=w["dt"],
                                 n_startup=4, precision=precision)
     ctx = L.Context(cfg, stream=stream)
+    device_bytes = L.lmvd_device_bytes(ctx.h)
     ctx.set_state({k: v.cuda() for k, v in st_host.items()})
+    torch.cuda.empty_cache()   # the staged input is no longer referenced
     for _ in range(args.warmup):
         ctx.advance_substage()
     ctx.synchronize()
@@ -244,7 +246,8 @@ def time_variant(L, w, precision, args, stream, st_host, local, ws, e2e_steps=0)
     L.lmvd_profile_enable(ctx.h, False)
     final = {k: v.cpu() for k, v in ctx.get_state().items()}
     ctx.synchronize()
-    res = dict(ms=ms, clocks=ck, launches=launches, prof=prof)
+    torch.cuda.empty_cache()
+    res = dict(ms=ms, clocks=ck, launches=launches, prof=prof, device_bytes=device_bytes)
     if e2e_steps > 0:
         host_in = {k: v.pin_memory() for k, v in st_host.items()}
         hist_dev = ctx.history_buffer()
@@ -443,6 +446,7 @@ def run_cuda(args):
         "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic (seeded Rayleigh-Taylor-shaped state)", "config": config,
         "clocks": res["clocks"], "gpu_launches": int(res["launches"]),
+        "device_bytes": res["device_bytes"],
         "roofline": roofline_of(prof, res["ms"], args.precision, (w["nx"], w["ny"], w["nz"])), "e2e": e2e,
         "kernels": breakdown,
     }
@@ -456,6 +460,7 @@ def run_cuda(args):
                           "FP32-FFT: double-float (2 x FP32, error-free transformations) transforms and products, "
                           "FP64 solves / RHS / update"),
             "value": v2, "unit": UNIT, "ms_per_step": r2["ms"] / args.steps, "clocks": r2["clocks"],
+            "device_bytes": r2["device_bytes"],
             "roofline": roofline_of(r2["prof"], r2["ms"], other, (w["nx"], w["ny"], w["nz"])),
             "kernels": {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps,
                             "tflops": (v[2] / (v[0] / 1e3) / 1e12) if v[0] > 0 else None}

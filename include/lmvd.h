@@ -67,6 +67,10 @@ extern "C" {
  *               by k) on m2^c and on m2^d, phi2 = 0 at y0 and y1 as the other two m2^d rows,
  *               Omega2 = 0, d<m1>/dy = d<m3>/dy = 0, dz/dy = 0, <m2^c>(y1) = 0. Both modes put the
  *               boundary rows first and last in each per-mode system and factor it without pivoting.
+ * memory_layout: 0 = automatic (the full layout unless its workspace would take more than 85% of the
+ *               free device memory), 1 = full, 2 = lean (6 instead of 8 physical work fields, products of
+ *               the RHS formed in three batches instead of two, a 2-field instead of 4-field transform
+ *               intermediate: the same results in about 27 GB less at 768 x 769 x 768).
  */
 typedef struct {
   int nx, ny, nz, spline_order;
@@ -78,12 +82,14 @@ typedef struct {
   int n_startup;
   int precision;
   int bc_mode;
+  int memory_layout;
 } lmvd_config;
 
 typedef struct lmvd_ctx lmvd_ctx;
 
 /* Fill *cfg with the defaults (p = 6, 2 pi periods, walls at -1 and +1, Re = 1000, Sc = Fr = 1,
- * density ratio 3, dt = 1e-3, kf = 4, beta_n = 0, beta_p = -4, n_startup = 20, precision = 0, bc_mode = 0) for
+ * density ratio 3, dt = 1e-3, kf = 4, beta_n = 0, beta_p = -4, n_startup = 20, precision = 0, bc_mode = 0,
+ * memory_layout = 0) for
  * the given grid.
  * Returns LMVD_ERR_INVALID_ARG if cfg is NULL. */
 int lmvd_default_config(lmvd_config* cfg, int nx, int ny, int nz);
@@ -207,6 +213,12 @@ int lmvd_adjoint_substage(lmvd_ctx* ctx, const void* state_bar_out, const void* 
  * Errors: INVALID_ARG (NULL), UNSUPPORTED (precision 1 or kf > 15), OOM, CUDA. */
 int lmvd_adjoint_startup(lmvd_ctx* ctx, const void* state_bar_out, const void* history_bar_out,
                          void* state_bar_in);
+
+/* Device memory (bytes) the context holds: its workspace (state, history, work fields, transform
+ * intermediate), the y-operators and their factors (the per-mode factors of the m^c and m2^d systems
+ * store only the band profile), the transform tables, and the adjoint workspace once an adjoint call has
+ * allocated it. 0 if ctx is NULL. (No paper counterpart: the HBM footprint of this implementation.) */
+size_t lmvd_device_bytes(const lmvd_ctx* ctx);
 
 /* Substage counter s (0 after a start-up). -1 if ctx is NULL. */
 int lmvd_substage_index(const lmvd_ctx* ctx);

@@ -43,6 +43,7 @@ struct AdjWork {
   // dz/dt before each start-up application (allocated on the first lmvd_adjoint_startup)
   cd* iterates = nullptr;
   int n_iterates = 0;
+  size_t small_bytes = 0;  // bytes of small
 };
 
 namespace {
@@ -155,7 +156,7 @@ __global__ void k_adj_update_means(Grid g, DBand B0gT, DLU lu, AdjUpd a) {
   for (int i = 0; i < ny; ++i) {  // U^T sweep
     double x = yb[i];
     for (int r = 1; r <= lu.K; ++r)
-      if (i - r >= 0) x -= lu.up[(i - r) * lu.K + r - 1] * win[r - 1];
+      if (i - r >= 0 && r <= lu.nu[i - r]) x -= lu_up(lu, i - r, r, 0) * win[r - 1];
     x *= lu.invd[i];
     for (int q = KMAX - 1; q > 0; --q) win[q] = win[q - 1];
     win[0] = x;
@@ -165,7 +166,7 @@ __global__ void k_adj_update_means(Grid g, DBand B0gT, DLU lu, AdjUpd a) {
   for (int i = ny - 1; i >= 0; --i) {  // L^T sweep
     double x = v[i];
     for (int q = 1; q <= lu.K; ++q)
-      if (i + q < ny) x -= lu.lo[(i + q) * lu.K + q - 1] * win[q - 1];
+      if (i + q < ny && q <= lu.nl[i + q]) x -= lu_lo(lu, i + q, q, 0) * win[q - 1];
     for (int q = KMAX - 1; q > 0; --q) win[q] = win[q - 1];
     win[0] = x;
     v[i] = x;
@@ -503,6 +504,7 @@ int adj_upload_band(AdjWork& A, const RowBand& m, DBand& d) {
   A.small.push_back(c0);
   if (cudaMalloc(&v, sizeof(double) * m.v.size()) != cudaSuccess) return LMVD_ERR_OOM;
   A.small.push_back(v);
+  A.small_bytes += sizeof(int) * m.c0.size() + sizeof(double) * m.v.size();
   if (cudaMemcpy(c0, m.c0.data(), sizeof(int) * m.c0.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(v, m.v.data(), sizeof(double) * m.v.size(), cudaMemcpyHostToDevice) != cudaSuccess)
     return LMVD_ERR_CUDA;
@@ -850,6 +852,12 @@ int copy_dflt(cudaStream_t st, void* dst, const void* src, size_t bytes) {
 }
 
 }  // namespace
+
+size_t adj_device_bytes(const Ctx& c) {
+  if (!c.adj) return 0;
+  const AdjWork& A = *c.adj;
+  return A.bytes + A.small_bytes + sizeof(cd) * c.g.ny * c.g.M * (size_t)A.n_iterates;
+}
 
 void adj_destroy(Ctx& c) {
   if (!c.adj) return;

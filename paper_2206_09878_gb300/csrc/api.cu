@@ -85,10 +85,22 @@ int cuda_check(Ctx& c) {
   return latch(c, e == cudaErrorMemoryAllocation ? LMVD_ERR_OOM : LMVD_ERR_CUDA);
 }
 
+// A device allocation owned by the context (freed by lmvd_destroy, counted by lmvd_device_bytes).
+int device_alloc(Ctx& c, void** p, size_t bytes) {
+  if (cudaMalloc(p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return LMVD_ERR_OOM;
+  }
+  c.small_allocs.push_back(*p);
+  c.small_bytes += bytes;
+  return LMVD_OK;
+}
+
 template <class T>
 int upload(Ctx& c, const std::vector<T>& h, T** d) {
-  if (cudaMalloc((void**)d, sizeof(T) * std::max<size_t>(1, h.size())) != cudaSuccess) return LMVD_ERR_OOM;
-  c.small_allocs.push_back(*d);
+  int e = device_alloc(c, (void**)d, sizeof(T) * std::max<size_t>(1, h.size()));
+  if (e) return e;
   if (!h.empty() && cudaMemcpy(*d, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice) != cudaSuccess)
     return LMVD_ERR_CUDA;
   return LMVD_OK;
@@ -116,16 +128,20 @@ int half_width(const RowBand& m) {
   return K;
 }
 
+// Shared factors keep the band layout of BandLU (K entries per row, zeros outside the profile).
 int upload_lu(Ctx& c, const BandLU& f, DLU& d) {
   double *lo, *up, *invd;
-  int *nl, *nu;
+  int *nl, *nu, *off;
+  std::vector<int> offs(f.n);
+  for (int i = 0; i < f.n; ++i) offs[i] = i * f.K;
   int e = upload(c, f.lo, &lo);
   if (!e) e = upload(c, f.up, &up);
   if (!e) e = upload(c, f.invd, &invd);
   if (!e) e = upload(c, f.nl, &nl);
   if (!e) e = upload(c, f.nu, &nu);
+  if (!e) e = upload(c, offs, &off);
   if (e) return e;
-  d = DLU{lo, up, invd, nl, nu, f.n, f.K, 0, 0.0};
+  d = DLU{lo, up, invd, nl, nu, off, off, f.n, f.K, 0, 0.0};
   for (int i = 0; i < f.n; ++i) d.flops_per_mode += 4.0 * (f.nl[i] + f.nu[i]) + 2.0;
   return LMVD_OK;
 }
@@ -213,24 +229,33 @@ int factor_per_mode(Ctx& c, const PerMode& pm, int K, DLU& out) {
     return LMVD_ERR_UNSUPPORTED;
   }
   const int n = pm.A2.n;
+  // only the profile is stored: row i's multipliers at lo_off[i].., its U entries at up_off[i]..
+  std::vector<int> lo_off(n), up_off(n);
+  size_t nlo = 0, nup = 0;
+  for (int i = 0; i < n; ++i) {
+    lo_off[i] = (int)nlo;
+    up_off[i] = (int)nup;
+    nlo += nl[i];
+    nup += nu[i];
+  }
   double *A2, *A0, *A1, *lo, *up, *invd;
-  int *dnl, *dnu;
+  int *dnl, *dnu, *dlo_off, *dup_off;
   int e = upload(c, pm.A2.a, &A2);
   if (!e) e = upload(c, pm.A0.a, &A0);
   if (!e) e = upload(c, pm.A1.a, &A1);
   if (!e) e = upload(c, nl, &dnl);
   if (!e) e = upload(c, nu, &dnu);
+  if (!e) e = upload(c, lo_off, &dlo_off);
+  if (!e) e = upload(c, up_off, &dup_off);
   if (e) return e;
   const size_t M = c.g.M;
-  if (cudaMalloc(&lo, sizeof(double) * (size_t)n * K * M) != cudaSuccess) return LMVD_ERR_OOM;
-  c.small_allocs.push_back(lo);
-  if (cudaMalloc(&up, sizeof(double) * (size_t)n * K * M) != cudaSuccess) return LMVD_ERR_OOM;
-  c.small_allocs.push_back(up);
-  if (cudaMalloc(&invd, sizeof(double) * (size_t)n * M) != cudaSuccess) return LMVD_ERR_OOM;
-  c.small_allocs.push_back(invd);
-  LMVD_LAUNCH(c, KC_MISC, 0, 8.0 * n * (2 * K + 1) * M, k_factor, mode_blocks(c.g), TPB_MODE, 0, c.g, n, K, A2, A0,
-              A1, dnl, dnu, lo, up, invd);
-  out = DLU{lo, up, invd, dnl, dnu, n, K, M, 0.0};
+  if (!(e = device_alloc(c, (void**)&lo, sizeof(double) * std::max<size_t>(nlo, 1) * M)) &&
+      !(e = device_alloc(c, (void**)&up, sizeof(double) * std::max<size_t>(nup, 1) * M)))
+    e = device_alloc(c, (void**)&invd, sizeof(double) * (size_t)n * M);
+  if (e) return e;
+  LMVD_LAUNCH(c, KC_MISC, 0, 8.0 * (nlo + nup + n) * M, k_factor, mode_blocks(c.g), TPB_MODE, 0, c.g, n, K, A2, A0,
+              A1, dnl, dnu, dlo_off, dup_off, lo, up, invd);
+  out = DLU{lo, up, invd, dnl, dnu, dlo_off, dup_off, n, K, M, 0.0};
   for (int i = 0; i < n; ++i) out.flops_per_mode += 4.0 * (nl[i] + nu[i]) + 2.0;
   return cuda_check(c);
 }
@@ -271,7 +296,7 @@ void carve(Ctx& c, Carver& cv) {
   c.r_om = cv.take<cd>(S);
   c.r_phi = cv.take<cd>(Sp);
   for (auto& p : c.sv) p = cv.take<cd>(S);
-  for (auto& p : c.st) p = cv.take<cd>(S);
+  for (int q = 0; q < 7; ++q) c.st[q] = c.sv[q];
   c.mm1 = cv.take<double>(ny);
   c.mm3 = cv.take<double>(ny);
   c.mm1_new = cv.take<double>(ny);
@@ -283,8 +308,8 @@ void carve(Ctx& c, Carver& cv) {
   c.invrho = cv.take<double>(P);
   c.fprime = cv.take<double>(P);
   for (auto& p : c.w) p = cv.take<double>(P);
-  for (auto& p : c.pw) p = cv.take<double>(P);
-  c.tbuf = cv.take<cd>((size_t)10 * ny * g.pz * (g.nx / 2));
+  for (int f = 0; f < PW_FIELDS; ++f) c.pw[f] = f < c.pw_n ? cv.take<double>(P) : nullptr;
+  c.tbuf = cv.take<cd>((size_t)c.tbuf_n * ny * g.pz * (g.nx / 2));
 }
 
 // ------------------------------------------------------------------ substage pieces
@@ -463,16 +488,27 @@ int advance_impl(Ctx& c, const Tape* tape) {
   const double* mcp[3] = {c.pw[0], c.pw[1], c.pw[2]};
   if (tape)
     for (int f = 0; f < 3; ++f) mcp[f] = tape->b[cf.kf][f];
-  // steps 4-5: products with m = m^d + m^c, forward transforms, RHS streams, collocation solves, RHS
-  P2Out q{};
-  for (int f = 0; f < 10; ++f) q.p[f] = c.pw[f];
-  if (cf.precision == 1)
-    LMVD_LAUNCH(c, KC_PRODUCTS, 18.0 * n, 8.0 * 18 * n, k_products_p2_df, elem_blocks(n), 256, 0, n, c.md[0],
-                c.md[1], c.md[2], mcp[0], mcp[1], mcp[2], c.rho, c.invrho, q);
-  else
-    LMVD_LAUNCH(c, KC_PRODUCTS, 18.0 * n, 8.0 * 18 * n, k_products_p2, elem_blocks(n), 256, 0, n, c.md[0], c.md[1],
-                c.md[2], mcp[0], mcp[1], mcp[2], c.rho, c.invrho, q);
-  fft_forward(c, c.pw, c.sv, 10);
+  // steps 4-5: products with m = m^d + m^c, forward transforms, RHS streams, collocation solves, RHS.
+  // The ten products are formed in batches (m^c may sit in pw[0..2]): with 8 work fields two batches
+  // of five in pw[3..7]; with 6, C11-C13 and C22-C33 in pw[3..5], then u and rho in pw[0..3] (each
+  // point's inputs are read before its outputs are written, so overwriting m^c there is safe).
+  struct Batch { int first, count, slot; };
+  const Batch full[2] = {{0, 5, 3}, {5, 5, 3}}, lean[3] = {{0, 3, 3}, {3, 3, 3}, {6, 4, 0}};
+  const Batch* batches = c.pw_n >= 8 ? full : lean;
+  const int nb = c.pw_n >= 8 ? 2 : 3;
+  for (int b = 0; b < nb; ++b) {
+    const Batch& bt = batches[b];
+    P2Out q{};
+    for (int f = 0; f < bt.count; ++f) q.p[bt.first + f] = c.pw[bt.slot + f];
+    const double fl = 1.8 * bt.count * n, by = 8.0 * (8 + bt.count) * n;
+    if (cf.precision == 1)
+      LMVD_LAUNCH(c, KC_PRODUCTS, fl, by, k_products_p2_df, elem_blocks(n), 256, 0, n, c.md[0], c.md[1], c.md[2],
+                  mcp[0], mcp[1], mcp[2], c.rho, c.invrho, q);
+    else
+      LMVD_LAUNCH(c, KC_PRODUCTS, fl, by, k_products_p2, elem_blocks(n), 256, 0, n, c.md[0], c.md[1], c.md[2],
+                  mcp[0], mcp[1], mcp[2], c.rho, c.invrho, q);
+    fft_forward(c, c.pw + bt.slot, c.sv + bt.first, bt.count);
+  }
   Fields10C svc{};
   for (int f = 0; f < 10; ++f) svc.p[f] = c.sv[f];
   Fields7 stw{};
@@ -554,6 +590,7 @@ bool valid_cfg(const lmvd_config& f) {
   if (!(f.dt > 0) || f.kf < 0 || f.n_startup < 0) return false;
   if (f.precision != 0 && f.precision != 1) return false;
   if (f.bc_mode != 0 && f.bc_mode != 1) return false;
+  if (f.memory_layout < 0 || f.memory_layout > 2) return false;
   return true;
 }
 
@@ -655,8 +692,19 @@ int lmvd_create(const lmvd_config* cfg, void* stream, lmvd_ctx** out) {
   }
   if (!err) err = fft_prepare(c);
   if (!err) {
+    // full layout if it takes at most 85% of the free device memory, else the lean one
     Carver probe{nullptr};
     carve(c, probe);
+    size_t free_b = 0, total_b = 0;
+    bool lean = cfg->memory_layout == 2;
+    if (cfg->memory_layout == 0)
+      lean = cudaMemGetInfo(&free_b, &total_b) == cudaSuccess && (double)probe.off > 0.85 * (double)free_b;
+    if (lean) {
+      c.pw_n = PW_LEAN;
+      c.tbuf_n = TBUF_LEAN;
+      probe = Carver{nullptr};
+      carve(c, probe);
+    }
     c.arena_bytes = probe.off;
     if (cudaMalloc(&c.arena, c.arena_bytes) != cudaSuccess) {
       cudaGetLastError();
@@ -858,6 +906,12 @@ int lmvd_adjoint_startup(lmvd_ctx* h, const void* sbar_out, const void* hbar_out
   if (!h || !sbar_out || !hbar_out || !sbar_in) return LMVD_ERR_INVALID_ARG;
   const int e = adjoint_startup(h->c, sbar_out, hbar_out, sbar_in);
   return e ? latch(h->c, e) : LMVD_OK;
+}
+
+size_t lmvd_device_bytes(const lmvd_ctx* h) {
+  if (!h) return 0;
+  const Ctx& c = h->c;
+  return c.arena_bytes + c.small_bytes + adj_device_bytes(c);
 }
 
 int lmvd_substage_index(const lmvd_ctx* h) { return h ? h->c.s : -1; }

@@ -6,10 +6,12 @@ namespace lmvd {
 
 // ------------------------------------------------------------------ band LU access
 __device__ inline double lu_lo(const DLU& f, int i, int q, int m) {
-  return __ldg(f.lo + (f.mstride ? ((size_t)(i * f.K + q - 1) * f.mstride + m) : (size_t)(i * f.K + q - 1)));
+  const size_t e = (size_t)__ldg(f.lo_off + i) + q - 1;
+  return __ldg(f.lo + (f.mstride ? e * f.mstride + m : e));
 }
 __device__ inline double lu_up(const DLU& f, int i, int r, int m) {
-  return __ldg(f.up + (f.mstride ? ((size_t)(i * f.K + r - 1) * f.mstride + m) : (size_t)(i * f.K + r - 1)));
+  const size_t e = (size_t)__ldg(f.up_off + i) + r - 1;
+  return __ldg(f.up + (f.mstride ? e * f.mstride + m : e));
 }
 __device__ inline double lu_invd(const DLU& f, int i, int m) {
   return __ldg(f.invd + (f.mstride ? ((size_t)i * f.mstride + m) : (size_t)i));
@@ -72,8 +74,8 @@ __device__ void band_solve_v(const DLU& f, int m, int comp, const V* in, const V
 }
 
 // Solve A^T x = in with the factors A = L U of A (no pivoting): A^T = U^T L^T, so a forward sweep with
-// U^T (lower triangular, diagonal of U) is followed by a backward sweep with L^T (unit upper). Entries of
-// the factors outside their profile are stored as zeros, so the sweeps run over K. Rows of the result
+// U^T (lower triangular, diagonal of U) is followed by a backward sweep with L^T (unit upper); column i
+// of U (of L) collects the entries of rows i - r (i + q) inside their profiles. Rows of the result
 // outside [zlo, zhi] are stored as zero (the recurrence itself uses the unmodified values). out may
 // alias in.
 template <class V>
@@ -85,7 +87,7 @@ __device__ void band_solve_T_v(const DLU& f, int m, int comp, const V* in, V* ou
     V v = in[vidx<V>(i, M, m, comp)];
 #pragma unroll
     for (int r = 1; r <= KMAX; ++r)
-      if (r <= f.K && i - r >= 0) v = vfma(-lu_up(f, i - r, r, m), win[r - 1], v);
+      if (r <= f.K && i - r >= 0 && r <= __ldg(f.nu + i - r)) v = vfma(-lu_up(f, i - r, r, m), win[r - 1], v);
     v = lu_invd(f, i, m) * v;
 #pragma unroll
     for (int q = KMAX - 1; q > 0; --q) win[q] = win[q - 1];
@@ -99,7 +101,7 @@ __device__ void band_solve_T_v(const DLU& f, int m, int comp, const V* in, V* ou
     V v = out[o];
 #pragma unroll
     for (int q = 1; q <= KMAX; ++q)
-      if (q <= f.K && i + q < f.n) v = vfma(-lu_lo(f, i + q, q, m), win[q - 1], v);
+      if (q <= f.K && i + q < f.n && q <= __ldg(f.nl + i + q)) v = vfma(-lu_lo(f, i + q, q, m), win[q - 1], v);
 #pragma unroll
     for (int q = KMAX - 1; q > 0; --q) win[q] = win[q - 1];
     win[0] = v;

@@ -376,6 +376,7 @@ int fft_prepare(Ctx& c) {
     c.small_allocs.push_back(p->tw);
     if (cudaMalloc(&p->twf, sizeof(float4) * p->n) != cudaSuccess) return LMVD_ERR_OOM;
     c.small_allocs.push_back(p->twf);
+    c.small_bytes += (sizeof(double2) + sizeof(float4)) * p->n;
     if (cudaMemcpy(p->tw, tw.data(), sizeof(double2) * p->n, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(p->twf, twf.data(), sizeof(float4) * p->n, cudaMemcpyHostToDevice) != cudaSuccess)
       return LMVD_ERR_CUDA;
@@ -397,8 +398,8 @@ static void inverse_t(Ctx& c, cd* const* in, void* const* out, int nf) {
   const Grid& g = c.g;
   const size_t tstride = (size_t)g.ny * g.pz * (g.nx / 2);
   C* T = reinterpret_cast<C*>(c.tbuf);
-  for (int f0 = 0; f0 < nf; f0 += 10) {
-    const int n = nf - f0 < 10 ? nf - f0 : 10;
+  for (int f0 = 0; f0 < nf; f0 += c.tbuf_n) {
+    const int n = nf - f0 < c.tbuf_n ? nf - f0 : c.tbuf_n;
     FieldsC fi{};
     FieldsRW fo{};
     for (int f = 0; f < n; ++f) {
@@ -428,8 +429,8 @@ static void forward_t(Ctx& c, void* const* in, cd* const* out, int nf) {
   const Grid& g = c.g;
   const size_t tstride = (size_t)g.ny * g.pz * (g.nx / 2);
   C* T = reinterpret_cast<C*>(c.tbuf);
-  for (int f0 = 0; f0 < nf; f0 += 10) {
-    const int n = nf - f0 < 10 ? nf - f0 : 10;
+  for (int f0 = 0; f0 < nf; f0 += c.tbuf_n) {
+    const int n = nf - f0 < c.tbuf_n ? nf - f0 : c.tbuf_n;
     FieldsRC fi{};
     FieldsW fo{};
     for (int f = 0; f < n; ++f) {

@@ -12,6 +12,14 @@
 namespace lmvd {
 
 constexpr int KMAX = 8;   // widest band (each side) of any y-system LU supported
+// Device-memory budget of one context: the transform intermediate holds up to TBUF_FIELDS fields
+// (transforms of more fields run in chunks), there are up to PW_FIELDS physical work fields, and the RHS
+// streams overwrite the first seven spectral value fields. When that layout would not leave room on the
+// device (768 x 769 x 768), lmvd_create uses the lean one: TBUF_LEAN and PW_LEAN fields.
+constexpr int TBUF_FIELDS = 4;
+constexpr int PW_FIELDS = 8;
+constexpr int TBUF_LEAN = 2;
+constexpr int PW_LEAN = 6;
 constexpr int WMAX = 9;   // widest row of a collocation matrix (spline order <= 9)
 
 // ---------------------------------------------------------------- complex helpers (FP64)
@@ -34,14 +42,18 @@ struct DBand {
   const double* v;
   int rows, w;
 };
-// LU factors of band systems. Shared factors: mstride = 0; per-mode factors: mstride = #modes and
-// element (i, q) of mode m at [(i * K + q) * mstride + m].
+// LU factors of band systems. Row i of L holds its nl[i] multipliers (q = 1..nl[i], multiplier of row
+// i - q) at entries lo_off[i] + q - 1, row i of U its nu[i] entries right of the diagonal at
+// up_off[i] + r - 1; only the profile is stored. Shared factors: mstride = 0, entry e at [e]; per-mode
+// factors: mstride = #modes, entry e of mode m at [e * mstride + m].
 struct DLU {
   const double* lo;
   const double* up;
   const double* invd;
   const int* nl;
   const int* nu;
+  const int* lo_off;
+  const int* up_off;
   int n, K;
   size_t mstride;
   double flops_per_mode;  // host-side: flops of one complex solve (sum over rows of 4 (nl + nu) + 2)
@@ -156,6 +168,7 @@ struct Ctx {
   void* arena = nullptr;
   size_t arena_bytes = 0;
   std::vector<void*> small_allocs;
+  size_t small_bytes = 0;  // bytes of small_allocs
 
   // state and history (spectral, B coefficients)
   cd *z, *om, *m2;
@@ -169,11 +182,12 @@ struct Ctx {
   cd *Rz, *zdot, *rt, *m1c, *m2c, *m3c, *r_om, *r_phi;
   double* r_m;        // 2 * ny
   cd* sv[10];         // spectral value fields at g (FFT outputs / inputs)
-  cd* st[7];          // RHS streams
-  cd* tbuf;           // FFT intermediate: up to 10 fields of ny * pz * (nx/2)
+  cd* st[7];          // RHS streams: the same memory as sv[0..6] (formed in place from sv)
+  cd* tbuf;           // FFT intermediate: tbuf_n fields of ny * pz * (nx/2)
   // physical
   double *md[3], *rho, *invrho, *fprime, *w[3];
-  double* pw[10];     // physical work fields
+  double* pw[PW_FIELDS];  // physical work fields (pw_n of them allocated)
+  int pw_n = PW_FIELDS, tbuf_n = TBUF_FIELDS;
 
   Prof prof;
   AdjWork* adj = nullptr;
@@ -186,6 +200,8 @@ int advance(Ctx& c, const Tape* tape);
 int startup_record(Ctx& c, const Tape* tape, cd* iterates);
 // one fixed-point application from zdot_in (api.cu), recording its physical fields a and b[3]
 int fp_record(Ctx& c, const cd* zdot_in, double* a, double* const* b);
+// device bytes held by the adjoint workspace (adjoint.cu; 0 before its first use)
+size_t adj_device_bytes(const Ctx& c);
 // adjoint of one substage (adjoint.cu); blobs as documented for lmvd_adjoint_substage
 int adjoint_substage(Ctx& c, const void* sbar_out, const void* hbar_out, void* sbar_in, void* hbar_in);
 // adjoint of the start-up (adjoint.cu); blobs as documented for lmvd_adjoint_startup

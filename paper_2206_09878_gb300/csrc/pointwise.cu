@@ -42,23 +42,24 @@ __global__ void k_product_L(size_t n, const double* w1, const double* w2, const 
     out[o] = -(w1[o] * m1[o] + w2[o] * m2[o] + w3[o] * m3[o]);
 }
 
-// m = m^d + m^c; outputs C11, C12, C13, C22, C23, C33 (C_ij = -m_i m_j / rho), u1, u2, u3 (u = m / rho), rho
+// m = m^d + m^c; outputs C11, C12, C13, C22, C23, C33 (C_ij = -m_i m_j / rho), u1, u2, u3 (u = m / rho), rho;
+// a null output pointer is skipped (the outputs are formed in batches)
 __global__ void k_products_p2(size_t n, const double* md1, const double* md2, const double* md3, const double* mc1,
                               const double* mc2, const double* mc3, const double* rho, const double* invrho, P2Out q) {
   for (size_t o = blockIdx.x * (size_t)blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x) {
     const double ir = invrho[o];
     const double a = md1[o] + mc1[o], b = md2[o] + mc2[o], c = md3[o] + mc3[o];
     const double ua = a * ir, ub = b * ir, uc = c * ir;
-    q.p[0][o] = -a * ua;
-    q.p[1][o] = -a * ub;
-    q.p[2][o] = -a * uc;
-    q.p[3][o] = -b * ub;
-    q.p[4][o] = -b * uc;
-    q.p[5][o] = -c * uc;
-    q.p[6][o] = ua;
-    q.p[7][o] = ub;
-    q.p[8][o] = uc;
-    q.p[9][o] = rho[o];
+    if (q.p[0]) q.p[0][o] = -a * ua;
+    if (q.p[1]) q.p[1][o] = -a * ub;
+    if (q.p[2]) q.p[2][o] = -a * uc;
+    if (q.p[3]) q.p[3][o] = -b * ub;
+    if (q.p[4]) q.p[4][o] = -b * uc;
+    if (q.p[5]) q.p[5][o] = -c * uc;
+    if (q.p[6]) q.p[6][o] = ua;
+    if (q.p[7]) q.p[7][o] = ub;
+    if (q.p[8]) q.p[8][o] = uc;
+    if (q.p[9]) q.p[9][o] = rho[o];
   }
 }
 
@@ -114,16 +115,16 @@ __global__ void k_products_p2_df(size_t n, const double* md1, const double* md2,
     const df ir = ld(invrho, o);
     const df a = dadd(ld(md1, o), ld(mc1, o)), b = dadd(ld(md2, o), ld(mc2, o)), c = dadd(ld(md3, o), ld(mc3, o));
     const df ua = dmul(a, ir), ub = dmul(b, ir), uc = dmul(c, ir);
-    st(q.p[0], o, dneg(dmul(a, ua)));
-    st(q.p[1], o, dneg(dmul(a, ub)));
-    st(q.p[2], o, dneg(dmul(a, uc)));
-    st(q.p[3], o, dneg(dmul(b, ub)));
-    st(q.p[4], o, dneg(dmul(b, uc)));
-    st(q.p[5], o, dneg(dmul(c, uc)));
-    st(q.p[6], o, ua);
-    st(q.p[7], o, ub);
-    st(q.p[8], o, uc);
-    st(q.p[9], o, ld(rho, o));
+    if (q.p[0]) st(q.p[0], o, dneg(dmul(a, ua)));
+    if (q.p[1]) st(q.p[1], o, dneg(dmul(a, ub)));
+    if (q.p[2]) st(q.p[2], o, dneg(dmul(a, uc)));
+    if (q.p[3]) st(q.p[3], o, dneg(dmul(b, ub)));
+    if (q.p[4]) st(q.p[4], o, dneg(dmul(b, uc)));
+    if (q.p[5]) st(q.p[5], o, dneg(dmul(c, uc)));
+    if (q.p[6]) st(q.p[6], o, ua);
+    if (q.p[7]) st(q.p[7], o, ub);
+    if (q.p[8]) st(q.p[8], o, uc);
+    if (q.p[9]) st(q.p[9], o, ld(rho, o));
   }
 }
 

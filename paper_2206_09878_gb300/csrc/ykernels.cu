@@ -287,7 +287,7 @@ __global__ void k_update_means(Grid g, DBand B0g, DLU lu_i, UpdateArgs a) {
     double v = 0.0;
     if (i > 0 && i < ny - 1) v = band_row_real(B0g, i, cur) + a.dt * (a.al * r[i] + a.be * rp[i]);
     const int nl = lu_i.nl[i];
-    for (int q = 1; q <= nl; ++q) v -= lu_i.lo[i * lu_i.K + q - 1] * win[q - 1];
+    for (int q = 1; q <= nl; ++q) v -= lu_lo(lu_i, i, q, 0) * win[q - 1];
     for (int q = KMAX - 1; q > 0; --q) win[q] = win[q - 1];
     win[0] = v;
     out[i] = v;
@@ -296,7 +296,7 @@ __global__ void k_update_means(Grid g, DBand B0g, DLU lu_i, UpdateArgs a) {
   for (int i = ny - 1; i >= 0; --i) {
     double v = out[i];
     const int nu = lu_i.nu[i];
-    for (int q = 1; q <= nu; ++q) v -= lu_i.up[i * lu_i.K + q - 1] * win[q - 1];
+    for (int q = 1; q <= nu; ++q) v -= lu_up(lu_i, i, q, 0) * win[q - 1];
     v *= lu_i.invd[i];
     for (int q = KMAX - 1; q > 0; --q) win[q] = win[q - 1];
     win[0] = v;
@@ -362,16 +362,18 @@ __global__ void k_sanitize(Grid g, int rows, cd* f, int zero_mean) {
 
 // ------------------------------------------------------------------ per-mode factorisation
 // LU (no pivoting) of A(k) = A2 - k^2 A0 + k A1 for every mode with k != 0; A2, A0, A1 in diagonal band
-// storage (half-width K, shared), profile nl/nu shared; factors stored per mode (stride M).
+// storage (half-width K, shared), profile nl/nu shared; the factors' profiles are stored per mode (stride
+// M) at the shared row offsets lo_off / up_off. k = 0 and Nyquist modes get identity factors.
 __global__ void k_factor(Grid g, int n, int K, const double* A2, const double* A0, const double* A1, const int* nl,
-                         const int* nu, double* lo, double* up, double* invd) {
+                         const int* nu, const int* lo_off, const int* up_off, double* lo, double* up, double* invd) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= (int)g.M) return;
   const size_t M = g.M;
   const int W = 2 * K + 1;
   if (m == 0 || is_nyquist(g, m)) {
     for (int i = 0; i < n; ++i) {
-      for (int q = 0; q < K; ++q) lo[(size_t)(i * K + q) * M + m] = up[(size_t)(i * K + q) * M + m] = 0.0;
+      for (int q = 1; q <= nl[i]; ++q) lo[(size_t)(lo_off[i] + q - 1) * M + m] = 0.0;
+      for (int r = 1; r <= nu[i]; ++r) up[(size_t)(up_off[i] + r - 1) * M + m] = 0.0;
       invd[(size_t)i * M + m] = 1.0;
     }
     return;
@@ -386,13 +388,12 @@ __global__ void k_factor(Grid g, int n, int K, const double* A2, const double* A
     for (int q = nl[i]; q >= 1; --q) {
       const int c = i - q;
       const double l = row[K - q] * invd[(size_t)c * M + m];
-      lo[(size_t)(i * K + q - 1) * M + m] = l;
+      lo[(size_t)(lo_off[i] + q - 1) * M + m] = l;
       row[K - q] = 0.0;
-      for (int r = 1; r <= nu[c]; ++r) row[K - q + r] -= l * up[(size_t)(c * K + r - 1) * M + m];
+      for (int r = 1; r <= nu[c]; ++r) row[K - q + r] -= l * up[(size_t)(up_off[c] + r - 1) * M + m];
     }
     invd[(size_t)i * M + m] = 1.0 / row[K];
-    for (int r = 1; r <= K; ++r) up[(size_t)(i * K + r - 1) * M + m] = r <= nu[i] ? row[K + r] : 0.0;
-    for (int q = nl[i] + 1; q <= K; ++q) lo[(size_t)(i * K + q - 1) * M + m] = 0.0;
+    for (int r = 1; r <= nu[i]; ++r) up[(size_t)(up_off[i] + r - 1) * M + m] = row[K + r];
   }
 }
 

@@ -31,7 +31,7 @@ class lmvd_config(ctypes.Structure):
                 ("rho_heavy", ctypes.c_double), ("rho_light", ctypes.c_double),
                 ("dt", ctypes.c_double), ("kf", ctypes.c_int), ("beta_n", ctypes.c_double),
                 ("beta_p", ctypes.c_double), ("n_startup", ctypes.c_int), ("precision", ctypes.c_int),
-                ("bc_mode", ctypes.c_int)]
+                ("bc_mode", ctypes.c_int), ("memory_layout", ctypes.c_int)]
 
 
 class LmvdError(RuntimeError):
@@ -70,6 +70,7 @@ def _load():
         "lmvd_state_bytes": (S, [P]),
         "lmvd_adjoint_substage": (I, [P, P, P, P, P]),
         "lmvd_adjoint_startup": (I, [P, P, P, P]),
+        "lmvd_device_bytes": (S, [P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -86,7 +87,7 @@ EXPORTED = ("lmvd_default_config", "lmvd_create", "lmvd_destroy", "lmvd_set_stat
             "lmvd_substage_index", "lmvd_synchronize", "lmvd_status", "lmvd_strerror", "lmvd_profile_enable",
             "lmvd_profile_read", "lmvd_kernel_class_name", "lmvd_kernel_launches", "lmvd_inverse_transform",
             "lmvd_forward_transform", "lmvd_inverse_transform_noalloc", "lmvd_state_bytes",
-            "lmvd_adjoint_substage", "lmvd_adjoint_startup")
+            "lmvd_adjoint_substage", "lmvd_adjoint_startup", "lmvd_device_bytes")
 LMVD_KERNEL_CLASSES = 13
 
 
@@ -216,6 +217,10 @@ def lmvd_state_bytes(h):
 def lmvd_adjoint_substage(h, state_bar_out, history_bar_out, state_bar_in, history_bar_in):
     _check(_lib.lmvd_adjoint_substage(h, _ptr(state_bar_out), _ptr(history_bar_out), _ptr(state_bar_in),
                                       _ptr(history_bar_in)), "lmvd_adjoint_substage")
+
+
+def lmvd_device_bytes(h):
+    return int(_lib.lmvd_device_bytes(h))
 
 
 def lmvd_adjoint_startup(h, state_bar_out, history_bar_out, state_bar_in):

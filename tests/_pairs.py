@@ -19,12 +19,12 @@ def oracle_config(w, **over):
     return Config(**c)
 
 
-def gpu_config(L, cfg, precision=0):
+def gpu_config(L, cfg, precision=0, memory_layout=0):
     return L.lmvd_default_config(cfg.nx, cfg.ny, cfg.nz, spline_order=cfg.p, lx=cfg.lx, lz=cfg.lz, y0=cfg.y0,
                                  y1=cfg.y1, re=cfg.re, sc=cfg.sc, fr=cfg.fr, rho_heavy=cfg.rho_h,
                                  rho_light=cfg.rho_l, dt=cfg.dt, kf=cfg.kf, beta_n=cfg.beta_n,
                                  beta_p=cfg.beta_p, n_startup=cfg.n_startup, precision=precision,
-                                 bc_mode=1 if cfg.bc == "potential" else 0)
+                                 bc_mode=1 if cfg.bc == "potential" else 0, memory_layout=memory_layout)
 
 
 def to_torch(st, device="cuda"):
@@ -55,12 +55,12 @@ def compare_states(S, gpu, ora):
     return e
 
 
-def make_pair(L, name, precision=0, **over):
+def make_pair(L, name, precision=0, memory_layout=0, **over):
     w = workload(name, **{k: v for k, v in over.items() if k in WORKLOADS[name]})
     cfg = oracle_config(w, **{k: v for k, v in over.items() if k not in WORKLOADS[name]})
     S = Substage(cfg)
     st = rt_state(**w)
-    ctx = L.Context(gpu_config(L, cfg, precision))
+    ctx = L.Context(gpu_config(L, cfg, precision, memory_layout))
     return S, ctx, st, cfg
 
 

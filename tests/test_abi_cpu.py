@@ -52,7 +52,7 @@ def test_config_struct_layout_matches(lib, tmp_path):
 
 @pytest.mark.parametrize("bad", [dict(nx=7), dict(ny=5), dict(spline_order=3), dict(dt=0.0), dict(re=-1.0),
                                  dict(y1=-2.0), dict(kf=-1), dict(precision=2),
-                                 dict(bc_mode=2), dict(bc_mode=-1)])
+                                 dict(bc_mode=2), dict(bc_mode=-1), dict(memory_layout=3)])
 def test_invalid_configs_rejected_without_gpu(lib, bad):
     cfg = lib.lmvd_default_config(32, 33, 32)
     for k, v in bad.items():

@@ -43,14 +43,16 @@ def _field_errors(L, S, ctx):
     ("rt32", {}),
     ("rt32", dict(nx=24, ny=21, nz=16, kmax=3)),
     ("rt32", dict(p=4, ny=25)),
+    ("rt32", dict(memory_layout=2)),
 ])
 def test_substages_match_oracle(L, name, over, precision):
-    """precision 0: FP64 throughout; 1: double-float transforms and products, FP64 spectral steps."""
+    """precision 0: FP64 throughout; 1: double-float transforms and products, FP64 spectral steps.
+    memory_layout 2: the lean workspace (three product batches, 2-field transform intermediate)."""
     from _pairs import compare_states, make_pair, to_numpy, to_torch
     S, ctx, st, cfg = make_pair(L, name, precision=precision, **over)
     S.set_state(**st)
     ctx.set_state(to_torch(st))
-    nsub = 2 * 5 if not over else 4
+    nsub = 2 * 5 if not over or "memory_layout" in over else 4
     worst = {}
     for s in range(nsub):
         S.advance_substage()
