@@ -68,9 +68,9 @@ extern "C" {
  *               Omega2 = 0, d<m1>/dy = d<m3>/dy = 0, dz/dy = 0, <m2^c>(y1) = 0. Both modes put the
  *               boundary rows first and last in each per-mode system and factor it without pivoting.
  * memory_layout: 0 = automatic (the full layout unless its workspace would take more than 85% of the
- *               free device memory), 1 = full, 2 = lean (6 instead of 8 physical work fields, products of
- *               the RHS formed in three batches instead of two, a 2-field instead of 4-field transform
- *               intermediate: the same results in about 27 GB less at 768 x 769 x 768).
+ *               free device memory), 1 = full, 2 = lean (6 instead of 10 physical work fields, the products
+ *               of the RHS formed in three batches instead of one, a 2-field instead of 4-field transform
+ *               intermediate: the same results in about 43 GB less at 768 x 769 x 768).
  */
 typedef struct {
   int nx, ny, nz, spline_order;
@@ -215,9 +215,9 @@ int lmvd_adjoint_startup(lmvd_ctx* ctx, const void* state_bar_out, const void* h
                          void* state_bar_in);
 
 /* Device memory (bytes) the context holds: its workspace (state, history, work fields, transform
- * intermediate), the y-operators and their factors (the per-mode factors of the m^c and m2^d systems
- * store only the band profile), the transform tables, and the adjoint workspace once an adjoint call has
- * allocated it. 0 if ctx is NULL. (No paper counterpart: the HBM footprint of this implementation.) */
+ * intermediate), the y-operators and their factors (the per-mode factors of the m^c and m2^d systems are
+ * stored for the kz >= 0 half-plane: they depend on kz^2 only), the transform tables, and the adjoint
+ * workspace once an adjoint call has allocated it. 0 if ctx is NULL. (No paper counterpart: the HBM footprint of this implementation.) */
 size_t lmvd_device_bytes(const lmvd_ctx* ctx);
 
 /* Substage counter s (0 after a start-up). -1 if ctx is NULL. */

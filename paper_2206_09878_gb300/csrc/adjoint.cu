@@ -102,7 +102,8 @@ __device__ void solve_T_job(const Grid& g, const DLU& lu, const SolveTJob& jb) {
     for (int i = 0; i < lu.n; ++i) out[vidx<V>(i, M, m, comp)] = vzero<V>();
     return;
   }
-  band_solve_T_v<V>(lu, m, comp, reinterpret_cast<const V*>(jb.in), out, M, jb.zlo, jb.zhi);
+  band_solve_T_v<V>(lu, m, lu.mstride ? factor_mode(g, m) : 0, comp, reinterpret_cast<const V*>(jb.in), out, M,
+                    jb.zlo, jb.zhi);
 }
 __global__ void k_solve_T_cd(Grid g, DLU lu, SolveTJobs jobs) { solve_T_job<cd>(g, lu, jobs.j[blockIdx.y]); }
 __global__ void k_solve_T_re(Grid g, DLU lu, SolveTJobs jobs) { solve_T_job<double>(g, lu, jobs.j[blockIdx.y]); }
@@ -156,7 +157,7 @@ __global__ void k_adj_update_means(Grid g, DBand B0gT, DLU lu, AdjUpd a) {
   for (int i = 0; i < ny; ++i) {  // U^T sweep
     double x = yb[i];
     for (int r = 1; r <= lu.K; ++r)
-      if (i - r >= 0 && r <= lu.nu[i - r]) x -= lu_up(lu, i - r, r, 0) * win[r - 1];
+      if (i - r >= 0) x -= lu_up(lu, i - r, r, 0) * win[r - 1];
     x *= lu.invd[i];
     for (int q = KMAX - 1; q > 0; --q) win[q] = win[q - 1];
     win[0] = x;
@@ -166,7 +167,7 @@ __global__ void k_adj_update_means(Grid g, DBand B0gT, DLU lu, AdjUpd a) {
   for (int i = ny - 1; i >= 0; --i) {  // L^T sweep
     double x = v[i];
     for (int q = 1; q <= lu.K; ++q)
-      if (i + q < ny && q <= lu.nl[i + q]) x -= lu_lo(lu, i + q, q, 0) * win[q - 1];
+      if (i + q < ny) x -= lu_lo(lu, i + q, q, 0) * win[q - 1];
     for (int q = KMAX - 1; q > 0; --q) win[q] = win[q - 1];
     win[0] = x;
     v[i] = x;

@@ -128,20 +128,16 @@ int half_width(const RowBand& m) {
   return K;
 }
 
-// Shared factors keep the band layout of BandLU (K entries per row, zeros outside the profile).
 int upload_lu(Ctx& c, const BandLU& f, DLU& d) {
   double *lo, *up, *invd;
-  int *nl, *nu, *off;
-  std::vector<int> offs(f.n);
-  for (int i = 0; i < f.n; ++i) offs[i] = i * f.K;
+  int *nl, *nu;
   int e = upload(c, f.lo, &lo);
   if (!e) e = upload(c, f.up, &up);
   if (!e) e = upload(c, f.invd, &invd);
   if (!e) e = upload(c, f.nl, &nl);
   if (!e) e = upload(c, f.nu, &nu);
-  if (!e) e = upload(c, offs, &off);
   if (e) return e;
-  d = DLU{lo, up, invd, nl, nu, off, off, f.n, f.K, 0, 0.0};
+  d = DLU{lo, up, invd, nl, nu, f.n, f.K, 0, 0.0};
   for (int i = 0; i < f.n; ++i) d.flops_per_mode += 4.0 * (f.nl[i] + f.nu[i]) + 2.0;
   return LMVD_OK;
 }
@@ -229,33 +225,23 @@ int factor_per_mode(Ctx& c, const PerMode& pm, int K, DLU& out) {
     return LMVD_ERR_UNSUPPORTED;
   }
   const int n = pm.A2.n;
-  // only the profile is stored: row i's multipliers at lo_off[i].., its U entries at up_off[i]..
-  std::vector<int> lo_off(n), up_off(n);
-  size_t nlo = 0, nup = 0;
-  for (int i = 0; i < n; ++i) {
-    lo_off[i] = (int)nlo;
-    up_off[i] = (int)nup;
-    nlo += nl[i];
-    nup += nu[i];
-  }
   double *A2, *A0, *A1, *lo, *up, *invd;
-  int *dnl, *dnu, *dlo_off, *dup_off;
+  int *dnl, *dnu;
   int e = upload(c, pm.A2.a, &A2);
   if (!e) e = upload(c, pm.A0.a, &A0);
   if (!e) e = upload(c, pm.A1.a, &A1);
   if (!e) e = upload(c, nl, &dnl);
   if (!e) e = upload(c, nu, &dnu);
-  if (!e) e = upload(c, lo_off, &dlo_off);
-  if (!e) e = upload(c, up_off, &dup_off);
   if (e) return e;
-  const size_t M = c.g.M;
-  if (!(e = device_alloc(c, (void**)&lo, sizeof(double) * std::max<size_t>(nlo, 1) * M)) &&
-      !(e = device_alloc(c, (void**)&up, sizeof(double) * std::max<size_t>(nup, 1) * M)))
-    e = device_alloc(c, (void**)&invd, sizeof(double) * (size_t)n * M);
+  // factors of the kz >= 0 half-plane (A(k) depends on kz^2): Mh = (nz/2 + 1) nxh factor modes
+  const size_t Mh = (size_t)(c.g.nz / 2 + 1) * c.g.nxh;
+  if (!(e = device_alloc(c, (void**)&lo, sizeof(double) * (size_t)n * K * Mh)) &&
+      !(e = device_alloc(c, (void**)&up, sizeof(double) * (size_t)n * K * Mh)))
+    e = device_alloc(c, (void**)&invd, sizeof(double) * (size_t)n * Mh);
   if (e) return e;
-  LMVD_LAUNCH(c, KC_MISC, 0, 8.0 * (nlo + nup + n) * M, k_factor, mode_blocks(c.g), TPB_MODE, 0, c.g, n, K, A2, A0,
-              A1, dnl, dnu, dlo_off, dup_off, lo, up, invd);
-  out = DLU{lo, up, invd, dnl, dnu, dlo_off, dup_off, n, K, M, 0.0};
+  LMVD_LAUNCH(c, KC_MISC, 0, 8.0 * n * (2 * K + 1) * Mh, k_factor, (unsigned)((Mh + TPB_MODE - 1) / TPB_MODE),
+              TPB_MODE, 0, c.g, n, K, A2, A0, A1, dnl, dnu, lo, up, invd);
+  out = DLU{lo, up, invd, dnl, dnu, n, K, Mh, 0.0};
   for (int i = 0; i < n; ++i) out.flops_per_mode += 4.0 * (nl[i] + nu[i]) + 2.0;
   return cuda_check(c);
 }
@@ -489,13 +475,13 @@ int advance_impl(Ctx& c, const Tape* tape) {
   if (tape)
     for (int f = 0; f < 3; ++f) mcp[f] = tape->b[cf.kf][f];
   // steps 4-5: products with m = m^d + m^c, forward transforms, RHS streams, collocation solves, RHS.
-  // The ten products are formed in batches (m^c may sit in pw[0..2]): with 8 work fields two batches
-  // of five in pw[3..7]; with 6, C11-C13 and C22-C33 in pw[3..5], then u and rho in pw[0..3] (each
-  // point's inputs are read before its outputs are written, so overwriting m^c there is safe).
+  // The ten products overwrite m^c where it sits in pw[0..2] (each point's inputs are read before its
+  // outputs are written): one batch into pw[0..9] in the full layout; in the lean one (6 work fields)
+  // C11-C13 and C22-C33 through pw[3..5], then u and rho into pw[0..3].
   struct Batch { int first, count, slot; };
-  const Batch full[2] = {{0, 5, 3}, {5, 5, 3}}, lean[3] = {{0, 3, 3}, {3, 3, 3}, {6, 4, 0}};
-  const Batch* batches = c.pw_n >= 8 ? full : lean;
-  const int nb = c.pw_n >= 8 ? 2 : 3;
+  const Batch full[1] = {{0, 10, 0}}, lean[3] = {{0, 3, 3}, {3, 3, 3}, {6, 4, 0}};
+  const Batch* batches = c.pw_n >= 10 ? full : lean;
+  const int nb = c.pw_n >= 10 ? 1 : 3;
   for (int b = 0; b < nb; ++b) {
     const Batch& bt = batches[b];
     P2Out q{};

@@ -5,16 +5,15 @@
 namespace lmvd {
 
 // ------------------------------------------------------------------ band LU access
-__device__ inline double lu_lo(const DLU& f, int i, int q, int m) {
-  const size_t e = (size_t)__ldg(f.lo_off + i) + q - 1;
-  return __ldg(f.lo + (f.mstride ? e * f.mstride + m : e));
+// element (i, q) of L, (i, r) of U, 1 / U(i, i) for factor mode mf (ignored for shared factors)
+__device__ inline double lu_lo(const DLU& f, int i, int q, int mf) {
+  return __ldg(f.lo + (f.mstride ? ((size_t)(i * f.K + q - 1) * f.mstride + mf) : (size_t)(i * f.K + q - 1)));
 }
-__device__ inline double lu_up(const DLU& f, int i, int r, int m) {
-  const size_t e = (size_t)__ldg(f.up_off + i) + r - 1;
-  return __ldg(f.up + (f.mstride ? e * f.mstride + m : e));
+__device__ inline double lu_up(const DLU& f, int i, int r, int mf) {
+  return __ldg(f.up + (f.mstride ? ((size_t)(i * f.K + r - 1) * f.mstride + mf) : (size_t)(i * f.K + r - 1)));
 }
-__device__ inline double lu_invd(const DLU& f, int i, int m) {
-  return __ldg(f.invd + (f.mstride ? ((size_t)i * f.mstride + m) : (size_t)i));
+__device__ inline double lu_invd(const DLU& f, int i, int mf) {
+  return __ldg(f.invd + (f.mstride ? ((size_t)i * f.mstride + mf) : (size_t)i));
 }
 
 // Banded solves with the LU factors, for right-hand sides stored complex [row][mode]. Every y-system
@@ -41,7 +40,7 @@ __device__ inline size_t vidx(int i, size_t M, int m, int comp) {
 
 // L U x = in, then out = x (+ add). out may alias in; add may be null.
 template <class V>
-__device__ void band_solve_v(const DLU& f, int m, int comp, const V* in, const V* add, V* out, size_t M) {
+__device__ void band_solve_v(const DLU& f, int m, int mf, int comp, const V* in, const V* add, V* out, size_t M) {
   V win[KMAX];
 #pragma unroll
   for (int q = 0; q < KMAX; ++q) win[q] = vzero<V>();
@@ -50,7 +49,7 @@ __device__ void band_solve_v(const DLU& f, int m, int comp, const V* in, const V
     const int nl = __ldg(f.nl + i);
 #pragma unroll
     for (int q = 1; q <= KMAX; ++q)
-      if (q <= nl) v = vfma(-lu_lo(f, i, q, m), win[q - 1], v);
+      if (q <= nl) v = vfma(-lu_lo(f, i, q, mf), win[q - 1], v);
 #pragma unroll
     for (int q = KMAX - 1; q > 0; --q) win[q] = win[q - 1];
     win[0] = v;
@@ -64,8 +63,8 @@ __device__ void band_solve_v(const DLU& f, int m, int comp, const V* in, const V
     const int nu = __ldg(f.nu + i);
 #pragma unroll
     for (int r = 1; r <= KMAX; ++r)
-      if (r <= nu) v = vfma(-lu_up(f, i, r, m), win[r - 1], v);
-    v = lu_invd(f, i, m) * v;
+      if (r <= nu) v = vfma(-lu_up(f, i, r, mf), win[r - 1], v);
+    v = lu_invd(f, i, mf) * v;
 #pragma unroll
     for (int q = KMAX - 1; q > 0; --q) win[q] = win[q - 1];
     win[0] = v;
@@ -74,12 +73,13 @@ __device__ void band_solve_v(const DLU& f, int m, int comp, const V* in, const V
 }
 
 // Solve A^T x = in with the factors A = L U of A (no pivoting): A^T = U^T L^T, so a forward sweep with
-// U^T (lower triangular, diagonal of U) is followed by a backward sweep with L^T (unit upper); column i
-// of U (of L) collects the entries of rows i - r (i + q) inside their profiles. Rows of the result
+// U^T (lower triangular, diagonal of U) is followed by a backward sweep with L^T (unit upper). Entries of
+// the factors outside their profile are stored as zeros, so the sweeps run over K. Rows of the result
 // outside [zlo, zhi] are stored as zero (the recurrence itself uses the unmodified values). out may
 // alias in.
 template <class V>
-__device__ void band_solve_T_v(const DLU& f, int m, int comp, const V* in, V* out, size_t M, int zlo, int zhi) {
+__device__ void band_solve_T_v(const DLU& f, int m, int mf, int comp, const V* in, V* out, size_t M, int zlo,
+                               int zhi) {
   V win[KMAX];
 #pragma unroll
   for (int q = 0; q < KMAX; ++q) win[q] = vzero<V>();
@@ -87,8 +87,8 @@ __device__ void band_solve_T_v(const DLU& f, int m, int comp, const V* in, V* ou
     V v = in[vidx<V>(i, M, m, comp)];
 #pragma unroll
     for (int r = 1; r <= KMAX; ++r)
-      if (r <= f.K && i - r >= 0 && r <= __ldg(f.nu + i - r)) v = vfma(-lu_up(f, i - r, r, m), win[r - 1], v);
-    v = lu_invd(f, i, m) * v;
+      if (r <= f.K && i - r >= 0) v = vfma(-lu_up(f, i - r, r, mf), win[r - 1], v);
+    v = lu_invd(f, i, mf) * v;
 #pragma unroll
     for (int q = KMAX - 1; q > 0; --q) win[q] = win[q - 1];
     win[0] = v;
@@ -101,7 +101,7 @@ __device__ void band_solve_T_v(const DLU& f, int m, int comp, const V* in, V* ou
     V v = out[o];
 #pragma unroll
     for (int q = 1; q <= KMAX; ++q)
-      if (q <= f.K && i + q < f.n && q <= __ldg(f.nl + i + q)) v = vfma(-lu_lo(f, i + q, q, m), win[q - 1], v);
+      if (q <= f.K && i + q < f.n) v = vfma(-lu_lo(f, i + q, q, mf), win[q - 1], v);
 #pragma unroll
     for (int q = KMAX - 1; q > 0; --q) win[q] = win[q - 1];
     win[0] = v;

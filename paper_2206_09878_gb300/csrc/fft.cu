@@ -20,7 +20,6 @@
 #include <cmath>
 #include <cstring>
 #include <mutex>
-#include <type_traits>
 
 #include "df64.h"
 #include "lmvd_internal.h"
@@ -103,16 +102,6 @@ struct FT<cdf> {
   __device__ static R rzero() { return df{0.f, 0.f}; }
 };
 
-// a + w b and a - w b (w = (wr, wi)) without forming w b: two FMA chains give the sum, 2a - sum the
-// difference: 6 FP64 instructions instead of 8 (a complex multiply and two complex adds). The difference
-// carries one more rounding of |a| than a - w b (a few 1e-16 relative).
-__device__ __forceinline__ void bfly_fma(cd a, cd b, double wr, double wi, cd& sum, cd& dif) {
-  sum.re = fma(-wi, b.im, fma(wr, b.re, a.re));
-  sum.im = fma(wi, b.re, fma(wr, b.im, a.im));
-  dif.re = fma(2.0, a.re, -sum.re);
-  dif.im = fma(2.0, a.im, -sum.im);
-}
-
 // One radix-R Stockham stage, in place in shared memory. The transform of length n is shared by
 // tpt = n / EPT threads; thread tt owns the butterflies tt, tt + tpt, ... (EPT / R of them), loads all
 // their inputs into registers, waits for the whole block, then writes the outputs back to the same
@@ -137,21 +126,6 @@ __device__ __forceinline__ void fft_stage(C* x, const FFTPlan& pl, int L, int tt
     const int b = tt + j * tpt;
     const int k = pow2 ? (b & (L - 1)) : (b % L);
     const int base = (b - k) * R + k;
-    if constexpr (R == 4 && std::is_same<C, cd>::value) {
-      if (k) {  // FP64 radix 4 with twiddles: 24 FP64 instructions (bfly_fma) instead of 28
-        const double2 w1 = pl.tw[k * tws], w2 = pl.tw[2 * k * tws], w3 = pl.tw[3 * k * tws];
-        cd t0, t1, t2, dd;
-        bfly_fma(v[j][0], v[j][2], w2.x, SIGN * w2.y, t0, t1);
-        const cd u1 = cmul(v[j][1], cd{w1.x, SIGN * w1.y});
-        bfly_fma(u1, v[j][3], w3.x, SIGN * w3.y, t2, dd);
-        const cd t3 = SIGN > 0 ? times_i(dd) : F::neg(times_i(dd));  // (SIGN i) (w1 v1 - w3 v3)
-        x[base] = t0 + t2;
-        x[base + L] = t1 + t3;
-        x[base + 2 * L] = t0 - t2;
-        x[base + 3 * L] = t1 - t3;
-        continue;
-      }
-    }
     if (k) {
 #pragma unroll
       for (int q = 1; q < R; ++q) v[j][q] = F::template mulw<SIGN>(v[j][q], pl, q * k * tws);

@@ -17,7 +17,7 @@ constexpr int KMAX = 8;   // widest band (each side) of any y-system LU supporte
 // streams overwrite the first seven spectral value fields. When that layout would not leave room on the
 // device (768 x 769 x 768), lmvd_create uses the lean one: TBUF_LEAN and PW_LEAN fields.
 constexpr int TBUF_FIELDS = 4;
-constexpr int PW_FIELDS = 8;
+constexpr int PW_FIELDS = 10;
 constexpr int TBUF_LEAN = 2;
 constexpr int PW_LEAN = 6;
 constexpr int WMAX = 9;   // widest row of a collocation matrix (spline order <= 9)
@@ -42,18 +42,16 @@ struct DBand {
   const double* v;
   int rows, w;
 };
-// LU factors of band systems. Row i of L holds its nl[i] multipliers (q = 1..nl[i], multiplier of row
-// i - q) at entries lo_off[i] + q - 1, row i of U its nu[i] entries right of the diagonal at
-// up_off[i] + r - 1; only the profile is stored. Shared factors: mstride = 0, entry e at [e]; per-mode
-// factors: mstride = #modes, entry e of mode m at [e * mstride + m].
+// LU factors of band systems, K entries per row (zeros outside the profile nl / nu). Shared factors:
+// mstride = 0, element (i, q) at [i * K + q]; per-mode factors: element (i, q) of factor mode mf at
+// [(i * K + q) * mstride + mf], where A(k) depends on kz only through kz^2, so only the modes with
+// kz >= 0 are stored (factor_mode): mstride = (nz/2 + 1) * nxh.
 struct DLU {
   const double* lo;
   const double* up;
   const double* invd;
   const int* nl;
   const int* nu;
-  const int* lo_off;
-  const int* up_off;
   int n, K;
   size_t mstride;
   double flops_per_mode;  // host-side: flops of one complex solve (sum over rows of 4 (nl + nu) + 2)
@@ -76,6 +74,14 @@ __device__ inline void wavenumbers(const Grid& g, int m, double& k1, double& k3)
   int kz = jz < g.nz / 2 ? jz : jz - g.nz;
   k1 = 6.283185307179586476925286766559 / g.lx * kx;
   k3 = 6.283185307179586476925286766559 / g.lz * kz;
+}
+
+// Index of mode m's per-mode factors: the mode with the same kx and |kz| (kz >= 0 half-plane).
+__device__ inline int factor_mode(const Grid& g, int m) {
+  int jz = m / g.nxh;
+  const int kx = m - jz * g.nxh;
+  if (jz > g.nz / 2) jz = g.nz - jz;
+  return jz * g.nxh + kx;
 }
 
 // Rows [r0, r1) of chunk c out of nc over `rows` rows (contiguous, sizes differing by at most one).

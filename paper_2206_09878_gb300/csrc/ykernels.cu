@@ -91,7 +91,8 @@ __device__ void solve_job(const Grid& g, const DLU& lu, const SolveJob& jb) {
     for (int i = 0; i < lu.n; ++i) out[vidx<V>(i, M, m, comp)] = vzero<V>();
     return;
   }
-  band_solve_v<V>(lu, m, comp, reinterpret_cast<const V*>(jb.in), reinterpret_cast<const V*>(jb.add), out, M);
+  band_solve_v<V>(lu, m, lu.mstride ? factor_mode(g, m) : 0, comp, reinterpret_cast<const V*>(jb.in),
+                  reinterpret_cast<const V*>(jb.add), out, M);
 }
 __global__ void k_solve_cd(Grid g, DLU lu, SolveJobs jobs) { solve_job<cd>(g, lu, jobs.j[blockIdx.y]); }
 __global__ void k_solve_re(Grid g, DLU lu, SolveJobs jobs) { solve_job<double>(g, lu, jobs.j[blockIdx.y]); }
@@ -361,25 +362,26 @@ __global__ void k_sanitize(Grid g, int rows, cd* f, int zero_mean) {
 }
 
 // ------------------------------------------------------------------ per-mode factorisation
-// LU (no pivoting) of A(k) = A2 - k^2 A0 + k A1 for every mode with k != 0; A2, A0, A1 in diagonal band
-// storage (half-width K, shared), profile nl/nu shared; the factors' profiles are stored per mode (stride
-// M) at the shared row offsets lo_off / up_off. k = 0 and Nyquist modes get identity factors.
+// LU (no pivoting) of A(k) = A2 - k^2 A0 + k A1 for the factor modes (kx, kz >= 0), mf = jz * nxh + kx,
+// jz = 0..nz/2 (stride Mh = (nz/2 + 1) nxh); A2, A0, A1 in diagonal band storage (half-width K, shared),
+// profile nl/nu shared; entries outside the profile are stored as zeros. k = 0 and Nyquist modes get
+// identity factors.
 __global__ void k_factor(Grid g, int n, int K, const double* A2, const double* A0, const double* A1, const int* nl,
-                         const int* nu, const int* lo_off, const int* up_off, double* lo, double* up, double* invd) {
-  const int m = blockIdx.x * blockDim.x + threadIdx.x;
-  if (m >= (int)g.M) return;
-  const size_t M = g.M;
+                         const int* nu, double* lo, double* up, double* invd) {
+  const size_t Mh = (size_t)(g.nz / 2 + 1) * g.nxh;
+  const int mf = blockIdx.x * blockDim.x + threadIdx.x;
+  if (mf >= (int)Mh) return;
+  const int jz = mf / g.nxh, kx = mf - jz * g.nxh;
   const int W = 2 * K + 1;
-  if (m == 0 || is_nyquist(g, m)) {
+  if (mf == 0 || kx == g.nx / 2 || jz == g.nz / 2) {
     for (int i = 0; i < n; ++i) {
-      for (int q = 1; q <= nl[i]; ++q) lo[(size_t)(lo_off[i] + q - 1) * M + m] = 0.0;
-      for (int r = 1; r <= nu[i]; ++r) up[(size_t)(up_off[i] + r - 1) * M + m] = 0.0;
-      invd[(size_t)i * M + m] = 1.0;
+      for (int q = 0; q < K; ++q) lo[(size_t)(i * K + q) * Mh + mf] = up[(size_t)(i * K + q) * Mh + mf] = 0.0;
+      invd[(size_t)i * Mh + mf] = 1.0;
     }
     return;
   }
-  double k1, k3;
-  wavenumbers(g, m, k1, k3);
+  const double k1 = 6.283185307179586476925286766559 / g.lx * kx;
+  const double k3 = 6.283185307179586476925286766559 / g.lz * jz;
   const double k2 = k1 * k1 + k3 * k3, k = sqrt(k2);
   double row[2 * KMAX + 1];
   for (int i = 0; i < n; ++i) {
@@ -387,13 +389,14 @@ __global__ void k_factor(Grid g, int n, int K, const double* A2, const double* A
       row[q] = A2[(size_t)i * W + q] - k2 * A0[(size_t)i * W + q] + k * A1[(size_t)i * W + q];
     for (int q = nl[i]; q >= 1; --q) {
       const int c = i - q;
-      const double l = row[K - q] * invd[(size_t)c * M + m];
-      lo[(size_t)(lo_off[i] + q - 1) * M + m] = l;
+      const double l = row[K - q] * invd[(size_t)c * Mh + mf];
+      lo[(size_t)(i * K + q - 1) * Mh + mf] = l;
       row[K - q] = 0.0;
-      for (int r = 1; r <= nu[c]; ++r) row[K - q + r] -= l * up[(size_t)(up_off[c] + r - 1) * M + m];
+      for (int r = 1; r <= nu[c]; ++r) row[K - q + r] -= l * up[(size_t)(c * K + r - 1) * Mh + mf];
     }
-    invd[(size_t)i * M + m] = 1.0 / row[K];
-    for (int r = 1; r <= nu[i]; ++r) up[(size_t)(up_off[i] + r - 1) * M + m] = row[K + r];
+    invd[(size_t)i * Mh + mf] = 1.0 / row[K];
+    for (int r = 1; r <= K; ++r) up[(size_t)(i * K + r - 1) * Mh + mf] = r <= nu[i] ? row[K + r] : 0.0;
+    for (int q = nl[i] + 1; q <= K; ++q) lo[(size_t)(i * K + q - 1) * Mh + mf] = 0.0;
   }
 }
 

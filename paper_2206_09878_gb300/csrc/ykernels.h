@@ -60,7 +60,7 @@ __global__ void k_backfill(size_t n, double c0, double c1, double c2, const cd* 
                            cd* h2);
 __global__ void k_sanitize(Grid g, int rows, cd* f, int zero_mean);
 __global__ void k_factor(Grid g, int n, int K, const double* A2, const double* A0, const double* A1, const int* nl,
-                         const int* nu, const int* lo_off, const int* up_off, double* lo, double* up, double* invd);
+                         const int* nu, double* lo, double* up, double* invd);
 
 // pointwise.cu: physical-space products (Sec. 2.1, 4.3, 5)
 struct EosArgs {

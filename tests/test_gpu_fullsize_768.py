@@ -33,8 +33,11 @@ def ops():
 
 
 def _run(L, precision):
+    import gc
     from _pairs import workload
     from paper_2206_09878_gb300.rt_inputs import rt_state
+    gc.collect()
+    torch.cuda.empty_cache()   # earlier tests' tensors, cached by torch, would not leave room for the context
     w = workload(W)
     cfg = L.lmvd_default_config(w["nx"], w["ny"], w["nz"], re=w["re"], rho_light=1.0 / w["ratio"], dt=w["dt"],
                                 n_startup=2, precision=precision)
