@@ -47,7 +47,13 @@ __device__ __forceinline__ df df_from_double_int(double x) {
   const int k = e - 1075;                                         // lo = rem * 2^k, k in [-178, 75]
   const int ka = k >> 1, kb = k - ka;                             // 2^ka, 2^kb are normal floats
   const float sa = __uint_as_float((unsigned)(ka + 127) << 23), sb = __uint_as_float((unsigned)(kb + 127) << 23);
-  float lo = __fmul_rn(__fmul_rn(__uint2float_rn((unsigned)(m52 & 0x1FFFFFFFull)), sa), sb);
+  // the low 29 mantissa bits as a float, rounded to nearest, on the FP32 pipe (an int-to-float
+  // conversion instruction would run at the FP64 rate): both 23-bit halves are exact through the 2^23
+  // trick (the float 2^23 + r has mantissa r), and one FMA rounds r1 2^23 + r0 once
+  const unsigned r = (unsigned)(m52 & 0x1FFFFFFFull);
+  const float f0 = __fsub_rn(__uint_as_float(0x4B000000u | (r & 0x7FFFFFu)), 8388608.0f);
+  const float f1 = __fsub_rn(__uint_as_float(0x4B000000u | (r >> 23)), 8388608.0f);
+  float lo = __fmul_rn(__fmul_rn(__fmaf_rn(f1, 8388608.0f, f0), sa), sb);
   lo = sign ? -lo : lo;
   float s, l;
   fast_two_sum(hi, lo, s, l);
