@@ -30,17 +30,21 @@ __host__ __device__ inline double df_to_double(df a) { return (double)a.hi + (do
 
 // Split of a double into hi + lo with integer operations only (no FP64 instruction): hi takes the
 // sign, exponent and the top 23 stored mantissa bits (truncation), lo the remaining 29 bits rounded
-// to 24 by one int-to-float conversion and scaled by two powers of two; a FastTwoSum renormalises.
-// Relative error <= 2^-48 for |x| >= 2^-102; smaller magnitudes keep hi exactly and lose lo gradually
-// (below 2^-126, outside the float range, the result is a signed zero). Magnitudes >= 2^128, inf and
-// nan take the FP64 conversion.
+// to 24 on the FP32 pipe and scaled by two powers of two; a FastTwoSum renormalises. Relative error
+// <= 2^-48 for |x| >= 2^-102; smaller magnitudes keep hi exactly and lose lo gradually (below 2^-126,
+// outside the float range, the result is a signed zero). Magnitudes >= 2^128 (outside the float range)
+// become a signed infinity, nan a nan. Every case stays off the FP64 pipe: the compiler may evaluate a
+// short branch for all threads, so even rare cases must not use FP64 instructions.
 __device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e);
 __device__ __forceinline__ df df_from_double_int(double x) {
   const unsigned long long u = (unsigned long long)__double_as_longlong(x);
   const unsigned hi32 = (unsigned)(u >> 32);
   const int e = (int)((hi32 >> 20) & 0x7ffu);
   const unsigned sign = hi32 & 0x80000000u;
-  if (e > 1150) return df_from_double(x);
+  if (e > 1150) {
+    const bool nan = e == 2047 && (u & 0xFFFFFFFFFFFFFull) != 0;
+    return df{__uint_as_float(nan ? 0x7FC00000u : (sign | 0x7F800000u)), 0.f};
+  }
   if (e < 897) return df{__uint_as_float(sign), 0.f};
   const unsigned long long m52 = u & 0xFFFFFFFFFFFFFull;
   const float hi = __uint_as_float(sign | ((unsigned)(e - 896) << 23) | (unsigned)(m52 >> 29));
@@ -63,13 +67,23 @@ __device__ __forceinline__ df df_from_double_int(double x) {
 // hi + lo rounded to a double with integer operations only (no FP64 instruction). The 24-bit
 // mantissa of lo is aligned to the 53-bit mantissa of hi and added (or subtracted); bits of lo below
 // the double's last place are rounded to nearest (a denormal lo is handled like a normal one).
-// Non-normal hi (denormal, inf, nan) takes the FP64 route.
+// Non-normal hi: inf and nan keep their value (lo is then irrelevant); a denormal hi (below 2^-126,
+// where lo of a normalised pair is zero) is converted exactly, with its leading bit found by clz.
 __device__ __forceinline__ double df_to_double_int(df a) {
   const unsigned hb = __float_as_uint(a.hi), lb = __float_as_uint(a.lo);
   const unsigned long long sgn = (unsigned long long)(hb & 0x80000000u) << 32;
   if ((hb & 0x7fffffffu) == 0) return __longlong_as_double((long long)sgn);  // a normalised pair has lo = 0 here
   int eh = (int)((hb >> 23) & 0xffu);
-  if (eh == 0 || eh == 255) return (double)a.hi + (double)a.lo;
+  if (eh == 255) {  // inf or nan
+    const unsigned long long mh = (unsigned long long)(hb & 0x7fffffu) << 29;
+    return __longlong_as_double((long long)(sgn | 0x7FF0000000000000ull | mh | (mh ? (1ull << 51) : 0ull)));
+  }
+  if (eh == 0) {  // denormal hi = m 2^-149, m < 2^23: leading bit at 31 - clz(m)
+    const unsigned m = hb & 0x7fffffu;
+    const int lead = 31 - __clz((int)m);                  // value = 1.f 2^(lead - 149)
+    const unsigned long long frac = ((unsigned long long)m << (52 - lead)) & 0xFFFFFFFFFFFFFull;
+    return __longlong_as_double((long long)(sgn | ((unsigned long long)(lead - 149 + 1023) << 52) | frac));
+  }
   unsigned long long M = (unsigned long long)((hb & 0x7fffffu) | 0x800000u) << 29;  // leading bit 52
   int el = (int)((lb >> 23) & 0xffu);
   if ((lb & 0x7fffffffu) != 0 && el != 255) {
