@@ -48,6 +48,15 @@ NCU_DRAM_BYTES_PER_UNIT = {(0, "fft_x_inverse", 768): 19983.0, (1, "fft_x_invers
 CPU_SAMPLE_N = 128
 
 
+def hbm_peak_gbs():
+    """Measured copy bandwidth of this machine's GB300 (MEASURED_PEAKS.json), else the stated fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -434,7 +443,8 @@ def run_cuda(args):
     prof = res["prof"]
     breakdown = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps,
                      "tflops": (v[2] / (v[0] / 1e3) / 1e12) if v[0] > 0 else None,
-                     "hbm_gbs": (v[3] / (v[0] / 1e3) / 1e9) if v[0] > 0 else None}
+                     "hbm_gbs": (v[3] / (v[0] / 1e3) / 1e9) if v[0] > 0 else None,
+                     "hbm_frac": (v[3] / (v[0] / 1e3) / 1e9 / hbm_peak_gbs()[0]) if v[0] > 0 else None}
                  for k, v in prof.items() if v[1] > 0}
     e2e = None
     if args.e2e_steps > 0:
@@ -449,6 +459,8 @@ def run_cuda(args):
         "device_bytes": res["device_bytes"],
         "roofline": roofline_of(prof, res["ms"], args.precision, (w["nx"], w["ny"], w["nz"])), "e2e": e2e,
         "kernels": breakdown,
+        "hbm_peak": {"gbs": hbm_peak_gbs()[0], "source": hbm_peak_gbs()[1],
+                     "note": "kernels[*].hbm_frac = algorithmic bytes / time / this copy bandwidth"},
     }
     if not args.no_variant:
         other = 1 - args.precision
