@@ -44,6 +44,7 @@ extern "C" {
 #define LMVD_ERR_OOM (-3)
 #define LMVD_ERR_NONFINITE (-4)
 #define LMVD_ERR_UNSUPPORTED (-5)
+#define LMVD_ERR_FP_DIVERGED (-6)
 
 /* Problem definition, copied at lmvd_create (all host values).
  * nx, nz      : Fourier grid (even; 3*nx/2 and 3*nz/2 must have no prime factors other than 2, 3).
@@ -223,11 +224,33 @@ size_t lmvd_device_bytes(const lmvd_ctx* ctx);
 /* Substage counter s (0 after a start-up). -1 if ctx is NULL. */
 int lmvd_substage_index(const lmvd_ctx* ctx);
 
-/* Block until all work of the context's stream is done; returns the latched status or CUDA. */
+/* Block until all work of the context's stream is done; returns the latched status or CUDA.
+ * Failure detection: every substage checks its new state on the device (inf or nan anywhere in z,
+ * Omega2, m2^d or the means sets a device status word, no host synchronisation); this call reads that
+ * word and latches LMVD_ERR_NONFINITE if it is set. */
 int lmvd_synchronize(lmvd_ctx* ctx);
 
-/* First error latched in the context (LMVD_OK if none). */
+/* First error latched in the context (LMVD_OK if none; a non-finite state is latched by the next
+ * lmvd_synchronize). */
 int lmvd_status(const lmvd_ctx* ctx);
+
+/* Diagnostics of the fixed-point iteration and of mass conservation (observability; the paper discusses
+ * convergence of the iteration in Sec. 3.1-3.2, Eq. y_k_delta, and instability when its iteration matrix
+ * has spectral radius >= 1). When enabled, each substage records on the device, without host
+ * synchronisation: the relative mass residual |rho_t + i k1 m1^c + i k3 m3^c + D* m2^c| / |rho_t| of its
+ * final m^c (B-coefficient space, all modes) and, for each of its k_f fixed-point applications, the
+ * relative change |dz/dt^{k+1} - dz/dt^k| / |dz/dt^{k+1}| (2-norms over all stored entries). If the last
+ * change is >= 1/2, the iteration did not converge: a device status bit is set and the next
+ * lmvd_synchronize latches LMVD_ERR_FP_DIVERGED. Enabling allocates a small record on the first call;
+ * the cost is one extra copy and read of dz/dt per application. Off by default.
+ * Errors: INVALID_ARG (NULL), OOM. */
+int lmvd_diagnostics_enable(lmvd_ctx* ctx, int on);
+
+/* Copies the record of the last substage (synchronous): out[0] = its substage index, out[1] = relative
+ * mass residual, out[2 + k] = relative change of application k + 1 (k < k_f). Writes min(n, 2 + k_f)
+ * values and returns 2 + k_f (the number available). The values are sums of atomics, not bitwise
+ * reproducible. Errors: INVALID_ARG (NULL, n < 0, diagnostics never enabled), CUDA. */
+int lmvd_diagnostics(lmvd_ctx* ctx, double* out, int n);
 
 /* Kernel accounting (no paper counterpart: observability of this implementation).
  * Every kernel the context enqueues belongs to one of LMVD_KERNEL_CLASSES classes

@@ -469,8 +469,23 @@ int advance_impl(Ctx& c, const Tape* tape) {
   LMVD_LAUNCH(c, KC_MISC, 16.0 * S, 80.0 * S, k_bdf, elem_blocks(S), 256, 0, S, a[0], a[1], a[2], a[3], 1.0 / cf.dt,
               c.z, c.zh[0], c.zh[1], c.zh[2], c.zdot);
   // step 3
-  for (int k = 0; k < cf.kf; ++k) fp_apply(c, tape ? tape->a[k] : nullptr, tape ? tape->b[k] : nullptr);
+  if (c.diag_on) cudaMemsetAsync(c.ddiag, 0, sizeof(double) * (2 * KF_MAX_ADJ + 4), c.stream);
+  for (int k = 0; k < cf.kf; ++k) {
+    // diagnostics: the change of this application (the previous iterate kept in sv[9], unused until pass 2)
+    if (c.diag_on && k < KF_MAX_ADJ + 1)
+      cudaMemcpyAsync(c.sv[9], c.zdot, sizeof(cd) * S, cudaMemcpyDeviceToDevice, c.stream);
+    fp_apply(c, tape ? tape->a[k] : nullptr, tape ? tape->b[k] : nullptr);
+    if (c.diag_on && k < KF_MAX_ADJ + 1)
+      LMVD_LAUNCH(c, KC_MISC, 6.0 * S, 32.0 * S, k_diff_norms, elem_blocks(S), 256, 0, S, c.zdot, c.sv[9],
+                  c.ddiag + 2 + 2 * k);
+  }
   mc_from_zdot(c, tape ? tape->a[cf.kf] : nullptr, tape ? tape->b[cf.kf] : nullptr);
+  if (c.diag_on) {
+    LMVD_LAUNCH(c, KC_MISC, 20.0 * S, 16.0 * 5 * S, k_mass_norms, elem_blocks(S), 256, 0, g, c.dstar, c.rt, c.m1c,
+                c.m2c, c.m3c, c.ddiag);
+    if (cf.kf <= KF_MAX_ADJ + 1)
+      LMVD_LAUNCH(c, KC_MISC, 0, 0, k_fp_check, 1, 1, 0, c.ddiag, cf.kf, c.dflags);
+  }
   const double* mcp[3] = {c.pw[0], c.pw[1], c.pw[2]};
   if (tape)
     for (int f = 0; f < 3; ++f) mcp[f] = tape->b[cf.kf][f];
@@ -531,6 +546,17 @@ int advance_impl(Ctx& c, const Tape* tape) {
     LMVD_LAUNCH(c, KC_UPDATE, Sp * (8.0 * c.Ss0.w + 10.0), 16.0 * 4 * Sp, k_update_m2_rhs,
                 dim3(mode_blocks(g), row_chunks(g, g.ny + 1)), TPB_MODE, 0, g, c.Ss0, c.Ss2, u);
     solve_modes(c, KC_UPDATE, {SolveJob{c.m2_new, nullptr, c.m2_new}}, c.lu_md);
+  }
+  // failure detection: any non-finite value in the new state sets the device status word
+  {
+    CheckJobs cj{};
+    cj.j[0] = CheckJob{reinterpret_cast<const double*>(c.z_new), 2 * S};
+    cj.j[1] = CheckJob{reinterpret_cast<const double*>(c.om_new), 2 * S};
+    cj.j[2] = CheckJob{reinterpret_cast<const double*>(c.m2_new), 2 * (S + g.M)};
+    cj.j[3] = CheckJob{c.mm1_new, (size_t)g.ny};
+    cj.j[4] = CheckJob{c.mm3_new, (size_t)g.ny};
+    LMVD_LAUNCH(c, KC_MISC, 0, 8.0 * (6 * S + 2 * g.M + 2 * g.ny), k_check_finite, dim3(elem_blocks(2 * S), 5), 256,
+                0, cj, c.dflags);
   }
   // history rotation (pointer swaps)
   cd* oldest = c.zh[2];
@@ -701,6 +727,8 @@ int lmvd_create(const lmvd_config* cfg, void* stream, lmvd_ctx** out) {
       carve(c, real);
     }
   }
+  if (!err && !(err = device_alloc(c, (void**)&c.dflags, sizeof(unsigned))))
+    cudaMemsetAsync(c.dflags, 0, sizeof(unsigned), c.stream);
   if (!err && cudaStreamSynchronize(c.stream) != cudaSuccess) err = LMVD_ERR_CUDA;
   if (err) {
     lmvd_destroy(h);
@@ -907,7 +935,42 @@ int lmvd_synchronize(lmvd_ctx* h) {
   Ctx& c = h->c;
   if (cudaStreamSynchronize(c.stream) != cudaSuccess) return latch(c, LMVD_ERR_CUDA);
   cuda_check(c);
+  unsigned flags = 0;
+  if (c.dflags && cudaMemcpy(&flags, c.dflags, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return latch(c, LMVD_ERR_CUDA);
+  if (flags & 1u) latch(c, LMVD_ERR_NONFINITE);
+  if (flags & 2u) latch(c, LMVD_ERR_FP_DIVERGED);
   return c.status;
+}
+
+int lmvd_diagnostics_enable(lmvd_ctx* h, int on) {
+  if (!h) return LMVD_ERR_INVALID_ARG;
+  Ctx& c = h->c;
+  if (on && !c.ddiag) {
+    const int e = device_alloc(c, (void**)&c.ddiag, sizeof(double) * (2 * KF_MAX_ADJ + 4));
+    if (e) return latch(c, e);
+    cudaMemsetAsync(c.ddiag, 0, sizeof(double) * (2 * KF_MAX_ADJ + 4), c.stream);
+  }
+  c.diag_on = on != 0;
+  return LMVD_OK;
+}
+
+int lmvd_diagnostics(lmvd_ctx* h, double* out, int n) {
+  if (!h || !out || n < 0) return LMVD_ERR_INVALID_ARG;
+  Ctx& c = h->c;
+  if (!c.ddiag) return LMVD_ERR_INVALID_ARG;
+  double rec[2 * KF_MAX_ADJ + 4];
+  if (cudaStreamSynchronize(c.stream) != cudaSuccess ||
+      cudaMemcpy(rec, c.ddiag, sizeof(rec), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return latch(c, LMVD_ERR_CUDA);
+  const int kf = std::min(c.cfg.kf, KF_MAX_ADJ + 1);
+  const int total = 2 + kf;
+  double vals[2 + KF_MAX_ADJ + 1];
+  vals[0] = c.s - 1;
+  vals[1] = rec[1] > 0 ? std::sqrt(rec[0] / rec[1]) : 0.0;
+  for (int k = 0; k < kf; ++k) vals[2 + k] = rec[3 + 2 * k] > 0 ? std::sqrt(rec[2 + 2 * k] / rec[3 + 2 * k]) : 0.0;
+  for (int q = 0; q < std::min(n, total); ++q) out[q] = vals[q];
+  return total;
 }
 
 int lmvd_status(const lmvd_ctx* h) { return h ? h->c.status : LMVD_ERR_INVALID_ARG; }
@@ -951,6 +1014,7 @@ const char* lmvd_strerror(int code) {
     case LMVD_ERR_CUDA: return "CUDA error";
     case LMVD_ERR_OOM: return "device out of memory";
     case LMVD_ERR_NONFINITE: return "non-finite value in the state";
+    case LMVD_ERR_FP_DIVERGED: return "fixed-point iteration did not converge";
     case LMVD_ERR_UNSUPPORTED: return "unsupported configuration";
     default: return "unknown error";
   }

@@ -197,6 +197,12 @@ struct Ctx {
 
   Prof prof;
   AdjWork* adj = nullptr;
+  unsigned* dflags = nullptr;  // device status word: bit 0 = a non-finite value in the state (k_check_finite),
+                               // bit 1 = the fixed point did not converge (diagnostics on)
+  // diagnostics record of the last substage (lmvd_diagnostics): [0, 1] = |mass residual|^2, |rho_t|^2,
+  // [2 + 2k, 3 + 2k] = |dz/dt^{k+1} - dz/dt^k|^2, |dz/dt^{k+1}|^2 for k < kf
+  bool diag_on = false;
+  double* ddiag = nullptr;
 };
 
 // one substage (api.cu); with a tape the physical fields the adjoint needs are kept

@@ -333,6 +333,72 @@ __global__ void k_update_m2_rhs(Grid g, DBand Ss0, DBand Ss2, UpdateArgs a) {
   }
 }
 
+// ------------------------------------------------------------------ failure detection
+// Sets bit 0 of *flag if array blockIdx.y of the job list holds a non-finite double (inf or nan: all
+// exponent bits set). Integer tests on the bit pattern keep this off the FP64 pipe; one atomic per warp.
+__global__ void k_check_finite(CheckJobs jobs, unsigned* flag) {
+  const CheckJob& jb = jobs.j[blockIdx.y];
+  bool bad = false;
+  for (size_t o = blockIdx.x * (size_t)blockDim.x + threadIdx.x; o < jb.n; o += (size_t)gridDim.x * blockDim.x)
+    bad |= (__double_as_longlong(jb.p[o]) & 0x7FF0000000000000ll) == 0x7FF0000000000000ll;
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1u);
+}
+
+// ------------------------------------------------------------------ diagnostics (lmvd_diagnostics)
+// Block sums then one atomicAdd per block (the record is not bitwise reproducible; it is diagnostic only).
+__device__ inline void block_add(double v, double* out) {
+  __shared__ double red[32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (threadIdx.x == 0) atomicAdd(out, v);
+  }
+}
+
+// out[0] += |a - b|^2, out[1] += |a|^2 over n complex entries
+__global__ void k_diff_norms(size_t n, const cd* a, const cd* b, double* out) {
+  double d = 0.0, s = 0.0;
+  for (size_t o = blockIdx.x * (size_t)blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x) {
+    const cd x = a[o], y = b[o];
+    const double dr = x.re - y.re, di = x.im - y.im;
+    d += dr * dr + di * di;
+    s += x.re * x.re + x.im * x.im;
+  }
+  block_add(d, out);
+  block_add(s, out + 1);
+}
+
+// Mass conservation of m^c in B-coefficient space (Sec. 4.2): out[0] += |rho_t + i k1 m1 + i k3 m3 + D* m2|^2,
+// out[1] += |rho_t|^2, over all rows and modes (k = 0 included: D* <m2^c> = -<rho_t>)
+__global__ void k_mass_norms(Grid g, const double* dstar, const cd* rt, const cd* m1, const cd* m2, const cd* m3,
+                             double* out) {
+  const size_t n = (size_t)g.ny * g.M;
+  double d = 0.0, s = 0.0;
+  for (size_t o = blockIdx.x * (size_t)blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x) {
+    const int m = (int)(o % g.M), i = (int)(o / g.M);
+    double k1, k3;
+    wavenumbers(g, m, k1, k3);
+    const cd r = rt[o];
+    const cd dm = __ldg(dstar + i) * (m2[o + g.M] - m2[o]);
+    const cd res = r + times_i(k1 * m1[o] + k3 * m3[o]) + dm;
+    d += res.re * res.re + res.im * res.im;
+    s += r.re * r.re + r.im * r.im;
+  }
+  block_add(d, out);
+  block_add(s, out + 1);
+}
+
+// bit 1 of *flag if the last (the kf-th) fixed-point application, recorded at diag[2 kf], diag[2 kf + 1],
+// still changed dz/dt by half its size or more
+__global__ void k_fp_check(const double* diag, int kf, unsigned* flag) {
+  if (kf < 1) return;
+  const double d = diag[2 * kf], s = diag[2 * kf + 1];
+  if (d >= 0.25 * s && d > 0.0) atomicOr(flag, 2u);
+}
+
 // ------------------------------------------------------------------ elementwise helpers
 // BDF-like guess (Eq. dzdt_guesses): zdot = (a0 z^s + a1 z^{s-1} + a2 z^{s-2} + a3 z^{s-3}) / dt.
 __global__ void k_bdf(size_t n, double a0, double a1, double a2, double a3, double idt, const cd* z, const cd* h0,

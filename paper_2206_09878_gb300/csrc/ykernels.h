@@ -41,6 +41,19 @@ struct UpdateArgs {
   double *mm1_new, *mm3_new;
 };
 
+struct CheckJob {
+  const double* p;
+  size_t n;  // doubles
+};
+struct CheckJobs {
+  CheckJob j[5];
+};
+__global__ void k_check_finite(CheckJobs jobs, unsigned* flag);
+__global__ void k_diff_norms(size_t n, const cd* a, const cd* b, double* out);
+__global__ void k_mass_norms(Grid g, const double* dstar, const cd* rt, const cd* m1, const cd* m2, const cd* m3,
+                             double* out);
+__global__ void k_fp_check(const double* diag, int kf, unsigned* flag);
+
 __global__ void k_eval_p1(Grid g, DBand B0g, DBand B1g, DBand B2g, DBand Sg0, DBand Sg1, const cd* z,
                           const cd* om, const cd* m2, const double* mm1, const double* mm3, Fields8 out);
 __global__ void k_eval(Grid g, EvalJobs jobs);

@@ -71,6 +71,8 @@ def _load():
         "lmvd_adjoint_substage": (I, [P, P, P, P, P]),
         "lmvd_adjoint_startup": (I, [P, P, P, P]),
         "lmvd_device_bytes": (S, [P]),
+        "lmvd_diagnostics_enable": (I, [P, I]),
+        "lmvd_diagnostics": (I, [P, ctypes.POINTER(ctypes.c_double), I]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -87,7 +89,8 @@ EXPORTED = ("lmvd_default_config", "lmvd_create", "lmvd_destroy", "lmvd_set_stat
             "lmvd_substage_index", "lmvd_synchronize", "lmvd_status", "lmvd_strerror", "lmvd_profile_enable",
             "lmvd_profile_read", "lmvd_kernel_class_name", "lmvd_kernel_launches", "lmvd_inverse_transform",
             "lmvd_forward_transform", "lmvd_inverse_transform_noalloc", "lmvd_state_bytes",
-            "lmvd_adjoint_substage", "lmvd_adjoint_startup", "lmvd_device_bytes")
+            "lmvd_adjoint_substage", "lmvd_adjoint_startup", "lmvd_device_bytes", "lmvd_diagnostics_enable",
+            "lmvd_diagnostics")
 LMVD_KERNEL_CLASSES = 13
 
 
@@ -217,6 +220,20 @@ def lmvd_state_bytes(h):
 def lmvd_adjoint_substage(h, state_bar_out, history_bar_out, state_bar_in, history_bar_in):
     _check(_lib.lmvd_adjoint_substage(h, _ptr(state_bar_out), _ptr(history_bar_out), _ptr(state_bar_in),
                                       _ptr(history_bar_in)), "lmvd_adjoint_substage")
+
+
+def lmvd_diagnostics_enable(h, on=True):
+    _check(_lib.lmvd_diagnostics_enable(h, 1 if on else 0), "lmvd_diagnostics_enable")
+
+
+def lmvd_diagnostics(h):
+    """dict(substage, mass_residual, fp_changes=[...]) of the last substage's record."""
+    buf = (ctypes.c_double * 18)()
+    n = _lib.lmvd_diagnostics(h, buf, 18)
+    if n < 0:
+        _check(n, "lmvd_diagnostics")
+    vals = list(buf)[:min(n, 18)]
+    return dict(substage=int(vals[0]), mass_residual=vals[1], fp_changes=vals[2:])
 
 
 def lmvd_device_bytes(h):

@@ -1,0 +1,83 @@
+"""GPU: failure detection and diagnostics, without faulting the GPU.
+
+* A non-finite value injected on the host into the state given to lmvd_set_state (nan in z, inf in Omega2)
+  propagates through a substage; the device check marks it and lmvd_synchronize returns
+  LMVD_ERR_NONFINITE (latched in lmvd_status). A clean run returns LMVD_OK.
+* The diagnostics record (lmvd_diagnostics) matches the oracle: the relative change of each fixed-point
+  application |dz/dt^{k+1} - dz/dt^k| / |dz/dt^{k+1}| is the oracle's fp_residuals (Sec. 3.1), and the
+  relative mass residual of m^c is at rounding level (Sec. 4.2, exact D*).
+* At density ratio 100 with a sharp interface the fixed point does not converge (the oracle shows
+  relative changes above 1 throughout); lmvd_synchronize returns LMVD_ERR_FP_DIVERGED. At the paper's
+  density ratios it stays clean.
+"""
+import numpy as np
+import pytest
+import torch
+
+pytestmark = pytest.mark.gpu
+
+NONFINITE, FP_DIVERGED = -4, -6
+
+
+@pytest.fixture(scope="module")
+def L():
+    assert torch.cuda.is_available()
+    from paper_2206_09878_gb300 import lmvd
+    return lmvd
+
+
+@pytest.mark.parametrize("field,value", [("z", np.nan), ("om", np.inf)])
+def test_nonfinite_state_is_detected(L, field, value):
+    from _pairs import make_pair, to_torch
+    S, ctx, st, cfg = make_pair(L, "rt32")
+    st = {k: v.copy() for k, v in st.items()}
+    st[field][cfg.ny // 2, 1, 1] = value
+    ctx.set_state(to_torch(st))
+    ctx.advance_substage()
+    assert L._lib.lmvd_synchronize(ctx.h) == NONFINITE
+    assert L.lmvd_status(ctx.h) == NONFINITE
+    ctx.close()
+
+
+def test_clean_run_reports_ok(L):
+    from _pairs import make_pair, to_torch
+    S, ctx, st, cfg = make_pair(L, "rt32")
+    L.lmvd_diagnostics_enable(ctx.h, True)
+    ctx.set_state(to_torch(st))
+    for _ in range(4):
+        ctx.advance_substage()
+    assert L._lib.lmvd_synchronize(ctx.h) == 0
+    ctx.close()
+
+
+def test_diagnostics_match_oracle(L):
+    from _pairs import make_pair, to_torch
+    S, ctx, st, cfg = make_pair(L, "rt32")
+    L.lmvd_diagnostics_enable(ctx.h, True)
+    S.set_state(**st)
+    ctx.set_state(to_torch(st))
+    for s in range(3):
+        S.advance_substage()
+        ctx.advance_substage()
+        d = L.lmvd_diagnostics(ctx.h)
+        print(s, d, S.fp_residuals)
+        assert d["substage"] == s
+        assert d["mass_residual"] < 1e-13
+        assert len(d["fp_changes"]) == cfg.kf
+        for g, o in zip(d["fp_changes"], S.fp_residuals):
+            assert abs(g - o) <= 1e-3 * o + 1e-11, (g, o)
+    ctx.close()
+
+
+def test_fp_divergence_is_detected(L):
+    """Density ratio 100, interface width 0.02 (beyond the paper's range): the iteration does not converge."""
+    from _pairs import make_pair, to_torch
+    S, ctx, st, cfg = make_pair(L, "rt32", ratio=100.0, width=0.02, n_startup=4)
+    L.lmvd_diagnostics_enable(ctx.h, True)
+    ctx.set_state(to_torch(st))
+    ctx.advance_substage()
+    d = L.lmvd_diagnostics(ctx.h)
+    print(d)
+    assert d["fp_changes"][-1] >= 0.5
+    assert L._lib.lmvd_synchronize(ctx.h) == FP_DIVERGED
+    ctx.close()
