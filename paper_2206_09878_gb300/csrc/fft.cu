@@ -174,10 +174,14 @@ __device__ void fft_inplace(C* x, const FFTPlan& pl, int tt, int tpt) {
   }
 }
 
+// Every pass kernel is bounded to 3 CTAs of 256 threads per SM (at most 85 registers per thread): the FP64
+// kernels would otherwise take ~100 registers and fit only 2 CTAs, and the third CTA's warps hide more of
+// the FP64 pipe's latency (1-3% faster FP64 passes at 512^3; the double-float kernels already fit 3).
+
 // ---------------------------------------------------------------- inverse z-pass
 // in: spectral value fields [ny][nz][nxh] (complex double); T: [f][ny][pz][nx/2] of C
 template <class C, int EPT>
-__global__ void k_fft_z_inv(FFTPlan pl, Grid g, FieldsC in, C* T, size_t tstride) {
+__global__ void __launch_bounds__(256, 3) k_fft_z_inv(FFTPlan pl, Grid g, FieldsC in, C* T, size_t tstride) {
   using F = FT<C>;
   extern __shared__ __align__(16) unsigned char sm_raw[];
   C* a = reinterpret_cast<C*>(sm_raw);
@@ -206,7 +210,7 @@ __global__ void k_fft_z_inv(FFTPlan pl, Grid g, FieldsC in, C* T, size_t tstride
 
 // ---------------------------------------------------------------- inverse x-pass (c2r, 2 rows per transform)
 template <class C, int EPT>
-__global__ void k_fft_x_inv(FFTPlan pl, Grid g, const C* T, size_t tstride, FieldsRW out) {
+__global__ void __launch_bounds__(256, 3) k_fft_x_inv(FFTPlan pl, Grid g, const C* T, size_t tstride, FieldsRW out) {
   using F = FT<C>;
   using R = typename F::R;
   extern __shared__ __align__(16) unsigned char sm_raw[];
@@ -247,7 +251,7 @@ __global__ void k_fft_x_inv(FFTPlan pl, Grid g, const C* T, size_t tstride, Fiel
 
 // ---------------------------------------------------------------- forward x-pass (r2c, 2 rows per transform)
 template <class C, int EPT>
-__global__ void k_fft_x_fwd(FFTPlan pl, Grid g, FieldsRC in, C* T, size_t tstride) {
+__global__ void __launch_bounds__(256, 3) k_fft_x_fwd(FFTPlan pl, Grid g, FieldsRC in, C* T, size_t tstride) {
   using F = FT<C>;
   using R = typename F::R;
   extern __shared__ __align__(16) unsigned char sm_raw[];
@@ -283,7 +287,7 @@ __global__ void k_fft_x_fwd(FFTPlan pl, Grid g, FieldsRC in, C* T, size_t tstrid
 
 // ---------------------------------------------------------------- forward z-pass (truncate, scale)
 template <class C, int EPT>
-__global__ void k_fft_z_fwd(FFTPlan pl, Grid g, const C* T, size_t tstride, FieldsW out) {
+__global__ void __launch_bounds__(256, 3) k_fft_z_fwd(FFTPlan pl, Grid g, const C* T, size_t tstride, FieldsW out) {
   using F = FT<C>;
   extern __shared__ __align__(16) unsigned char sm_raw[];
   C* a = reinterpret_cast<C*>(sm_raw);
