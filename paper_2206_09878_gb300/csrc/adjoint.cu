@@ -684,6 +684,7 @@ void fp_step_T(Ctx& c, AdjWork& A, const double* a_tape, double* const* b_tape);
 int pass1_T(Ctx& c, AdjWork& A);
 
 int adjoint_impl(Ctx& c) {
+  NvtxRange range("lmvd adjoint substage");
   AdjWork& A = *c.adj;
   const Grid& g = c.g;
   const lmvd_config& cf = c.cfg;
@@ -821,6 +822,7 @@ int pass1_T(Ctx& c, AdjWork& A) {
 // zh_q = z - c_q dt zdot, zdot_prev = zdot (c_q = 1/2, 1, 3/2), RHS_prev = 0, with zdot after n_startup
 // applications from 0. Each application's physical fields are re-recorded from its stored iterate.
 int adjoint_startup_impl(Ctx& c) {
+  NvtxRange range("lmvd adjoint start-up");
   AdjWork& A = *c.adj;
   const Grid& g = c.g;
   const lmvd_config& cf = c.cfg;

@@ -432,6 +432,7 @@ void fp_apply(Ctx& c, double* a = nullptr, double* const* b = nullptr) {
 // tape (optional): records the physical z fields of pass 1; iterates (optional): receives dz/dt before each
 // application, n_startup consecutive spectral fields (the adjoint re-records each application from these).
 void startup(Ctx& c, const Tape* tape = nullptr, cd* iterates = nullptr) {
+  NvtxRange range("lmvd start-up");
   const size_t S = (size_t)c.g.ny * c.g.M;
   physical_pass_1(c, tape ? tape->zp : nullptr);
   cudaMemsetAsync(c.zdot, 0, sizeof(cd) * S, c.stream);
@@ -456,7 +457,9 @@ int advance_impl(Ctx& c, const Tape* tape) {
   const size_t S = (size_t)g.ny * g.M;
   const size_t n = (size_t)g.ny * g.P;
   const bool stage_n = (c.s % 2) == 0;
+  NvtxRange substage_range("lmvd substage (Algorithm 2)");
   // steps 1-2
+  NvtxRange pass1_range("steps 1-2: m^d, pass 1, R_z, BDF guess");
   physical_pass_1(c, tape ? tape->zp : nullptr);
   double a[4];
   if (stage_n) {
@@ -469,6 +472,8 @@ int advance_impl(Ctx& c, const Tape* tape) {
   LMVD_LAUNCH(c, KC_MISC, 16.0 * S, 80.0 * S, k_bdf, elem_blocks(S), 256, 0, S, a[0], a[1], a[2], a[3], 1.0 / cf.dt,
               c.z, c.zh[0], c.zh[1], c.zh[2], c.zdot);
   // step 3
+  nvtxRangePop();
+  nvtxRangePushA("step 3: fixed point, m^c");
   if (c.diag_on) cudaMemsetAsync(c.ddiag, 0, sizeof(double) * (2 * KF_MAX_ADJ + 4), c.stream);
   for (int k = 0; k < cf.kf; ++k) {
     // diagnostics: the change of this application (the previous iterate kept in sv[9], unused until pass 2)
@@ -489,6 +494,8 @@ int advance_impl(Ctx& c, const Tape* tape) {
   const double* mcp[3] = {c.pw[0], c.pw[1], c.pw[2]};
   if (tape)
     for (int f = 0; f < 3; ++f) mcp[f] = tape->b[cf.kf][f];
+  nvtxRangePop();
+  nvtxRangePushA("steps 4-5: pass 2, RHS");
   // steps 4-5: products with m = m^d + m^c, forward transforms, RHS streams, collocation solves, RHS.
   // The ten products overwrite m^c where it sits in pw[0..2] (each point's inputs are read before its
   // outputs are written): one batch into pw[0..9] in the full layout; in the lean one (6 work fields)
@@ -526,6 +533,8 @@ int advance_impl(Ctx& c, const Tape* tape) {
   LMVD_LAUNCH(c, KC_RHS_EVAL, S * (4.0 * 6 * c.B1g.w + 4.0), 16.0 * 9 * S, k_rhs_eval,
               dim3(mode_blocks(g), row_chunks(g, g.ny + 1)), TPB_MODE, 0,
               g, c.B1g, c.B2g, c.Bs[0], c.Bs[1], c.Bs[2], c.Bs[3], stc, c.r_om, c.r_phi, c.r_m);
+  nvtxRangePop();
+  nvtxRangePushA("step 6: RK2 update");
   // step 6: midpoint RK2, low-storage: (al, be) = (1/2, 0) at stage n, (1, -1/2) at stage '
   UpdateArgs u{};
   u.dt = cf.dt;

@@ -6,6 +6,8 @@
 #include <cstdint>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/lmvd.h"
 #include "df64.h"
 
@@ -125,6 +127,17 @@ struct FFTPlan {
   double scale_d = 1.0;    // 1 / (px pz) for the forward z-pass
   df scale_f{1.f, 0.f};
   df s3f{0.f, 0.f};        // sin(2 pi / 3) as a double-float
+};
+
+// ---------------------------------------------------------------- tracing
+// NVTX range (visible to ncu / nsys; a no-op without an attached tool) around host-side enqueueing of a
+// step of Algorithm 2. advance_impl opens one inner range and, at each step boundary, pops it and pushes
+// the next step's, so the inner object's destructor closes the last one (also on an early return).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
 };
 
 // ---------------------------------------------------------------- per-class launch accounting
