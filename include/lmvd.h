@@ -5,7 +5,9 @@
  * Algorithm 2: m^d from Eq. phi_poisson / md_recon, R_z and the BDF-like guess of
  * Eq. dzdt_guesses, k_f fixed-point applications of L (Eq. y_k, Sec. 4.3), m^c from
  * Eq. COM_fourier / CF_fourier / mc_recon / mc_mean, the right-hand sides of Eq. DNS_system,
- * and the segregated midpoint RK2 update (Sec. 3.3).
+ * and the segregated midpoint RK2 update (Sec. 3.3). The adjoints of a substage and of the start-up
+ * (the differentiation path) and a double-float precision path for the transforms and products are
+ * part of the same library.
  *
  * Conventions shared by every call
  * --------------------------------
@@ -18,7 +20,8 @@
  * The plane means <m1>, <m3> are float64 vectors of ny B-spline coefficients.
  * y-basis: clamped B-splines on uniform breakpoints of [y0, y1] (Appendix C), order p for all
  * fields but m2 and order p + 1 for m2, collocated at Greville abscissae.
- * Walls at y0 and y1 are no-slip; dz/dy = 0 there.
+ * Boundaries at y0 and y1: no-slip walls or the paper's potential matching (lmvd_config.bc_mode);
+ * dz/dy = 0 there in both.
  *
  * Pointers passed to set/get calls may be device memory or host memory (pinned host memory
  * gives asynchronous copies); they are read or written on the context's stream with
@@ -50,7 +53,7 @@ extern "C" {
  * nx, nz      : Fourier grid (even; 3*nx/2 and 3*nz/2 must have no prime factors other than 2, 3).
  * ny          : number of order-p B-splines in y (>= p + 4).
  * spline_order: p (4 .. 8).
- * lx, lz      : periods in x and z;  y0 < y1: wall positions.
+ * lx, lz      : periods in x and z;  y0 < y1: the boundaries in y.
  * re, sc, fr  : Reynolds, Schmidt, Froude numbers: mu = 1/re, rho D_z = 1/(re sc), g = 1/fr^2 along -y.
  * rho_heavy, rho_light: densities of the pure fluids; EOS rho = rl rh / (rh - (rh - rl) z) (Sec. 5).
  * dt          : time step of one RK2 step (two substages).
