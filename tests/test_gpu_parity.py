@@ -44,6 +44,8 @@ def _field_errors(L, S, ctx):
     ("rt32", dict(nx=24, ny=21, nz=16, kmax=3)),
     ("rt32", dict(p=4, ny=25)),
     ("rt32", dict(memory_layout=2)),
+    ("rt32", dict(nx=12, ny=11, nz=24, p=5, kmax=2)),    # 18-point x transforms: 6 elements per thread
+    ("rt32", dict(nx=8, ny=10, nz=8, p=4, kmax=2)),      # 12-point transforms: one thread per transform
 ])
 def test_substages_match_oracle(L, name, over, precision):
     """precision 0: FP64 throughout; 1: double-float transforms and products, FP64 spectral steps.
