@@ -70,6 +70,7 @@ def parse():
     ap.add_argument("--no-variant", action="store_true", help="skip timing the other precision")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/forward cost ratio")
     ap.add_argument("--adjoint-workload", default="rt128")
+    ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT comparison of the transforms")
     return ap.parse_args()
 
 
@@ -359,6 +360,57 @@ def adjoint_ratio(L, name, stream, reps=3):
             "gradient": gradient_ratio(L, name, stream)}
 
 
+def cufft_comparison(L, w, stream, df_prof=None, steps=None, kf=4, reps=5):
+    """Per-field time of the 3/2-rule synthesis and analysis at the bench grid: this library's FP64 passes
+    (lmvd_inverse_transform / lmvd_forward_transform, 4 fields per call) and, as the comparison baseline,
+    cuFFT through torch.fft (irfft2 / rfft2 of the zero-padded field, padding outside the timed region)
+    in FP64 and FP32. The double-float per-field times come from the precision-1 run's kernel profile
+    (8 + 4 (kf + 1) inverse and 12 + 2 kf forward fields per substage)."""
+    import torch
+    nx, ny, nz = w["nx"], w["ny"], w["nz"]
+    px, pz, nxh = 3 * nx // 2, 3 * nz // 2, nx // 2 + 1
+    cfg = L.lmvd_default_config(nx, ny, nz, n_startup=0)
+    ctx = L.Context(cfg, stream=stream)
+    nf = 4
+    out = {}
+    with torch.cuda.stream(stream):
+        spec = torch.randn(nf, ny, nz, nxh, dtype=torch.complex128, device="cuda")
+        phys = torch.empty(nf, ny, pz, px, dtype=torch.float64, device="cuda")
+
+        def timed(fn, per):
+            fn()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) / reps / per
+
+        out["lmvd_fp64_inverse"] = timed(lambda: L.lmvd_inverse_transform(ctx.h, spec, phys, nf), nf)
+        out["lmvd_fp64_forward"] = timed(lambda: L.lmvd_forward_transform(ctx.h, phys, spec, nf), nf)
+        del spec, phys
+        ctx.close()
+        torch.cuda.empty_cache()
+        for name, cdt, rdt in (("fp64", torch.complex128, torch.float64), ("fp32", torch.complex64, torch.float32)):
+            padded = torch.randn(ny, pz, px // 2 + 1, dtype=cdt, device="cuda")
+            real = torch.randn(ny, pz, px, dtype=rdt, device="cuda")
+            # unnormalised both ways (no separate scaling kernel), the padding done outside the timed region:
+            # cuFFT's most favourable form of the same synthesis / analysis
+            out["cufft_%s_inverse" % name] = timed(lambda: torch.fft.irfft2(padded, s=(pz, px), norm="forward"), 1)
+            out["cufft_%s_forward" % name] = timed(lambda: torch.fft.rfft2(real, norm="backward"), 1)
+            del padded, real
+            torch.cuda.empty_cache()
+    if df_prof and steps:
+        n_inv, n_fwd = 8 + 4 * (kf + 1), 12 + 2 * kf
+        out["lmvd_df_inverse"] = (df_prof["fft_z_inverse"][0] + df_prof["fft_x_inverse"][0]) / steps / n_inv
+        out["lmvd_df_forward"] = (df_prof["fft_x_forward"][0] + df_prof["fft_z_forward"][0]) / steps / n_fwd
+    return {"unit": "ms per field", "grid": [nx, ny, nz], "padded": [px, ny, pz], **out,
+            "note": "cuFFT transforms the whole padded field; this library skips the zero padding and the "
+                    "truncated modes and pairs two real rows per complex transform"}
+
+
 def gradient_ratio(L, name, stream, rk_steps=20, every_steps=5):
     """The whole gradient of the adjoint configuration against its forward: start-up (n_startup = 20) and
     2 rk_steps substages from an initial state without history; the gradient runs that forward keeping a
@@ -479,6 +531,9 @@ def run_cuda(args):
                         for k, v in r2["prof"].items() if v[1] > 0},
             "state_rel_l2_vs_headline_after_%d_substages" % (args.warmup + args.steps): errs,
         }
+    if rank == 0 and ws == 1 and not args.no_cufft:
+        df_prof = prof if args.precision == 1 else (None if args.no_variant else r2["prof"])
+        out["cufft_baseline"] = cufft_comparison(L, w, stream, df_prof, args.steps)
     if rank == 0 and ws == 1 and not args.no_adjoint:
         out["adjoint"] = adjoint_ratio(L, args.adjoint_workload, stream)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
