@@ -156,21 +156,6 @@ __device__ __forceinline__ df ddot2(df a, df b, df c, df d) {
   fast_two_sum(s, t, r, rl);
   return df{r, rl};
 }
-// 1 / a: float estimate refined by one Newton step in df arithmetic (relative error ~2^-46)
-__device__ __forceinline__ df drcp(df a) {
-  const float q1 = __frcp_rn(a.hi);
-  // r = 1 - a q1 evaluated in df: a.hi q1 = p + e exactly
-  const float p = __fmul_rn(a.hi, q1);
-  const float e = __fmaf_rn(a.hi, q1, -p);
-  float r = __fsub_rn(1.0f, p);  // exact: p is within a few ulp of 1
-  r = __fsub_rn(r, e);
-  r = __fmaf_rn(-a.lo, q1, r);
-  const float q2 = __fmul_rn(q1, r);
-  float s, sl;
-  fast_two_sum(q1, q2, s, sl);
-  return df{s, sl};
-}
-
 // complex helpers
 __device__ __forceinline__ cdf cadd(cdf a, cdf b) { return cdf{dadd(a.re, b.re), dadd(a.im, b.im)}; }
 __device__ __forceinline__ cdf csub(cdf a, cdf b) { return cdf{dsub(a.re, b.re), dsub(a.im, b.im)}; }

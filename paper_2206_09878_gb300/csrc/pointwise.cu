@@ -75,18 +75,20 @@ __global__ void k_products_p1_df(size_t n, EosArgs e, const double* zp, const do
                                  const double* zy, const double* lapz, const double* m1, const double* m2,
                                  const double* m3, double* rho, double* invrho, double* fprime, double* w1,
                                  double* w2, double* w3, double* rz) {
-  const df rh = df_from_double(e.rh);
-  const df drho = df_from_double(e.rh - e.rl);
-  const df irlrh = df_from_double(1.0 / (e.rl * e.rh));
-  const df cfp = df_from_double((e.rh - e.rl) / (e.rl * e.rh));
+  const double irlrh = 1.0 / (e.rl * e.rh);
+  const double drho = e.rh - e.rl;
   const df kap = df_from_double(e.kappa);
   for (size_t o = blockIdx.x * (size_t)blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x) {
-    const df ir = dmul(dsub(rh, dmul(drho, ld(zp, o))), irlrh);
-    const df r = drcp(ir);
+    // the EOS itself (1/rho, rho, f') in FP64 from z rounded to a double; the results are split back into
+    // double-float pairs for the products (both conversions on the integer pipe)
+    const double zd = df_to_double_int(ld(zp, o));
+    const double ird = (e.rh - drho * zd) * irlrh;
+    const double rd = 1.0 / ird;
+    const df ir = df_from_double_int(ird);
     const df gx = ld(zx, o), gy = ld(zy, o), gz = ld(zz, o);
-    st(rho, o, r);
+    st(rho, o, df_from_double_int(rd));
     st(invrho, o, ir);
-    st(fprime, o, dmul(dmul(r, r), cfp));
+    st(fprime, o, df_from_double_int(rd * rd * drho * irlrh));
     st(w1, o, dmul(gx, ir));
     st(w2, o, dmul(gy, ir));
     st(w3, o, dmul(gz, ir));
