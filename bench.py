@@ -71,6 +71,7 @@ def parse():
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/forward cost ratio")
     ap.add_argument("--adjoint-workload", default="rt128")
     ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT comparison of the transforms")
+    ap.add_argument("--no-graphs", action="store_true", help="skip the eager / CUDA-graph comparison")
     return ap.parse_args()
 
 
@@ -411,6 +412,42 @@ def cufft_comparison(L, w, stream, df_prof=None, steps=None, kf=4, reps=5):
                     "truncated modes and pairs two real rows per complex transform"}
 
 
+def graphs_comparison(L, stream, grids=((32, 33, 32), (64, 65, 64), (128, 129, 128)), substages=40):
+    """ms per substage with eager launches and with CUDA-graph replay (lmvd_graphs_enable) on small,
+    launch-bound grids (the 32 x 33 x 32 recipe, resized); 20 warm-up substages capture all 10 launch
+    patterns first."""
+    import numpy as np
+    import torch
+    from paper_2206_09878_gb300.rt_inputs import WORKLOADS, rt_state
+    out = {}
+    for nx, ny, nz in grids:
+        w = dict(WORKLOADS["rt32"], nx=nx, ny=ny, nz=nz)
+        row = {}
+        for graphs in (False, True):
+            cfg = L.lmvd_default_config(w["nx"], w["ny"], w["nz"], re=w["re"], rho_light=1.0 / w["ratio"],
+                                        dt=w["dt"], n_startup=4)
+            ctx = L.Context(cfg, stream=stream)
+            L.lmvd_graphs_enable(ctx.h, graphs)
+            with torch.cuda.stream(stream):
+                ctx.set_state({k: torch.from_numpy(np.ascontiguousarray(v)).cuda()
+                               for k, v in rt_state(**w).items()})
+                for _ in range(20):
+                    ctx.advance_substage()
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(substages):
+                    ctx.advance_substage()
+                e1.record(stream)
+                torch.cuda.synchronize()
+            row["graph_ms" if graphs else "eager_ms"] = e0.elapsed_time(e1) / substages
+            if graphs:
+                row["graphs_held"] = L.lmvd_graph_count(ctx.h)
+            ctx.close()
+        out["%dx%dx%d" % (nx, ny, nz)] = row
+    return out
+
+
 def gradient_ratio(L, name, stream, rk_steps=20, every_steps=5):
     """The whole gradient of the adjoint configuration against its forward: start-up (n_startup = 20) and
     2 rk_steps substages from an initial state without history; the gradient runs that forward keeping a
@@ -534,6 +571,8 @@ def run_cuda(args):
     if rank == 0 and ws == 1 and not args.no_cufft:
         df_prof = prof if args.precision == 1 else (None if args.no_variant else r2["prof"])
         out["cufft_baseline"] = cufft_comparison(L, w, stream, df_prof, args.steps)
+    if rank == 0 and ws == 1 and not args.no_graphs:
+        out["graphs"] = graphs_comparison(L, stream)
     if rank == 0 and ws == 1 and not args.no_adjoint:
         out["adjoint"] = adjoint_ratio(L, args.adjoint_workload, stream)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

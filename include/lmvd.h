@@ -138,6 +138,20 @@ int lmvd_advance_substage(lmvd_ctx* ctx);
 /* nsteps RK2 steps = 2 * nsteps substages. Errors as lmvd_advance_substage. */
 int lmvd_step(lmvd_ctx* ctx, int nsteps);
 
+/* CUDA graphs for lmvd_advance_substage / lmvd_step (no paper counterpart: launch overhead of this
+ * implementation). When on (the default), a substage is captured into a CUDA graph the first time its
+ * launch pattern occurs and replayed afterwards; the pattern is the stage (n or '), the diagnostics flag
+ * and which internal buffer holds which state and history field, so a run meets 10 patterns (the
+ * z history cycles through five buffers, the other fields through two). Results are those of the
+ * eager launches (same kernels, same arguments, same order). Substages run eagerly while per-launch
+ * profiling is on, inside the adjoint's recording, on the legacy default stream (ctx created with a
+ * NULL stream), or after a capture was refused. Off: eager launches, the graphs are released.
+ * Errors: INVALID_ARG (NULL). */
+int lmvd_graphs_enable(lmvd_ctx* ctx, int on);
+
+/* Number of substage graphs the context holds (-1 if ctx is NULL). */
+int lmvd_graph_count(const lmvd_ctx* ctx);
+
 /* Intermediate fields of the last substage, for testing and diagnostics (B coefficients unless
  * stated): which = LMVD_FIELD_*. out: caller-owned host or device buffer of lmvd_field_bytes().
  * Errors: INVALID_ARG (unknown field, NULL), CUDA. */
@@ -265,7 +279,8 @@ int lmvd_diagnostics(lmvd_ctx* ctx, double* out, int n);
  *   last enable: out4[0] total kernel milliseconds (CUDA events; 0 when profiling is off),
  *   out4[1] launches, out4[2] algorithmic flops, out4[3] algorithmic DRAM bytes (the minimum
  *   traffic of each launch: its inputs read once and its outputs written once).
- * lmvd_kernel_launches(ctx): kernels enqueued since lmvd_create (-1 if ctx is NULL).
+ * lmvd_kernel_launches(ctx): kernels enqueued since lmvd_create, those of replayed graphs included
+ *   (-1 if ctx is NULL).
  * Errors: INVALID_ARG (NULL ctx or out4, cls out of range), CUDA. */
 #define LMVD_KERNEL_CLASSES 13
 int lmvd_profile_enable(lmvd_ctx* ctx, int on);

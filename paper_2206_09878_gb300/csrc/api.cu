@@ -451,7 +451,9 @@ void startup(Ctx& c, const Tape* tape = nullptr, cd* iterates = nullptr) {
   c.s = 0;
 }
 
-int advance_impl(Ctx& c, const Tape* tape) {
+// Enqueues the kernels of one substage on c.stream (no host synchronisation, no allocation: the sequence
+// can be captured into a CUDA graph); rotate_history() then advances the host-side buffer assignment.
+void enqueue_substage(Ctx& c, const Tape* tape) {
   const Grid& g = c.g;
   const lmvd_config& cf = c.cfg;
   const size_t S = (size_t)g.ny * g.M;
@@ -567,7 +569,10 @@ int advance_impl(Ctx& c, const Tape* tape) {
     LMVD_LAUNCH(c, KC_MISC, 0, 8.0 * (6 * S + 2 * g.M + 2 * g.ny), k_check_finite, dim3(elem_blocks(2 * S), 5), 256,
                 0, cj, c.dflags);
   }
-  // history rotation (pointer swaps)
+}
+
+// history rotation (pointer swaps): z cycles through five buffers, the other pairs swap
+void rotate_history(Ctx& c) {
   cd* oldest = c.zh[2];
   c.zh[2] = c.zh[1];
   c.zh[1] = c.zh[0];
@@ -583,6 +588,96 @@ int advance_impl(Ctx& c, const Tape* tape) {
   std::swap(c.r_phi_prev, c.r_phi);
   std::swap(c.r_m_prev, c.r_m);
   c.s += 1;
+}
+
+// What decides the launch sequence of a substage besides the configuration: the stage, the diagnostics
+// flag and which buffer plays which role. z rotates with period 5 and the pairs with period 2, so a run
+// meets 10 keys.
+void graph_key(const Ctx& c, const void** k) {
+  const void* p[Ctx::GRAPH_KEY] = {c.z, c.z_new, c.zh[0], c.zh[1], c.zh[2], c.om, c.om_new, c.m2, c.m2_new,
+                                   c.mm1, c.mm1_new, c.mm3, c.mm3_new, c.zdot, c.zdot_prev, c.r_om, c.r_om_prev,
+                                   c.r_phi, c.r_phi_prev, c.r_m, c.r_m_prev,
+                                   reinterpret_cast<const void*>((uintptr_t)(c.s & 1)),
+                                   reinterpret_cast<const void*>((uintptr_t)c.diag_on)};
+  for (int i = 0; i < Ctx::GRAPH_KEY; ++i) k[i] = p[i];
+}
+
+void graphs_clear(Ctx& c) {
+  for (auto& G : c.graphs) cudaGraphExecDestroy(G.exec);
+  c.graphs.clear();
+}
+
+// Capture the substage's launches into a graph (nothing runs during the capture) and instantiate it;
+// the launch accounting it enqueued is kept with the graph and added at every replay.
+Ctx::SubstageGraph* graph_capture(Ctx& c) {
+  if (c.graphs.size() >= 32) graphs_clear(c);
+  Ctx::SubstageGraph G{};
+  graph_key(c, G.key);
+  const Prof before = c.prof;
+  if (cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  enqueue_substage(c, nullptr);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(c.stream, &graph);
+  G.launches = c.prof.launches - before.launches;
+  for (int k = 0; k < KC_COUNT; ++k) {
+    G.n[k] = c.prof.n[k] - before.n[k];
+    G.flops[k] = c.prof.flops[k] - before.flops[k];
+    G.bytes[k] = c.prof.bytes[k] - before.bytes[k];
+  }
+  c.prof.launches = before.launches;
+  for (int k = 0; k < KC_COUNT; ++k) {
+    c.prof.n[k] = before.n[k];
+    c.prof.flops[k] = before.flops[k];
+    c.prof.bytes[k] = before.bytes[k];
+  }
+  if (e != cudaSuccess || !graph) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    return nullptr;
+  }
+  const cudaError_t ei = cudaGraphInstantiate(&G.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ei != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  c.graphs.push_back(G);
+  return &c.graphs.back();
+}
+
+Ctx::SubstageGraph* graph_find(Ctx& c) {
+  const void* k[Ctx::GRAPH_KEY];
+  graph_key(c, k);
+  for (auto& G : c.graphs)
+    if (std::equal(k, k + Ctx::GRAPH_KEY, G.key)) return &G;
+  return nullptr;
+}
+
+int advance_impl(Ctx& c, const Tape* tape) {
+  // the graph path: not with a tape (adjoint recording), not while profiling (its events time each
+  // launch), not on the legacy default stream (it cannot be captured)
+  if (c.graphs_on && !tape && !c.prof.on && c.stream) {
+    Ctx::SubstageGraph* G = graph_find(c);
+    if (!G) G = graph_capture(c);
+    if (G) {
+      NvtxRange range("lmvd substage (graph)");
+      if (cudaGraphLaunch(G->exec, c.stream) != cudaSuccess) return latch(c, LMVD_ERR_CUDA);
+      c.prof.launches += G->launches;
+      for (int k = 0; k < KC_COUNT; ++k) {
+        c.prof.n[k] += G->n[k];
+        c.prof.flops[k] += G->flops[k];
+        c.prof.bytes[k] += G->bytes[k];
+      }
+      rotate_history(c);
+      return cuda_check(c);
+    }
+    c.graphs_on = false;  // capture refused: eager launches from here on
+  }
+  enqueue_substage(c, tape);
+  rotate_history(c);
   return cuda_check(c);
 }
 
@@ -753,6 +848,7 @@ void lmvd_destroy(lmvd_ctx* h) {
   if (c.stream) cudaStreamSynchronize(c.stream);
   else cudaDeviceSynchronize();
   adj_destroy(c);
+  graphs_clear(c);
   for (auto& p : c.prof.pending) {
     cudaEventDestroy(p.a);
     cudaEventDestroy(p.b);
@@ -841,6 +937,16 @@ int lmvd_step(lmvd_ctx* h, int nsteps) {
   }
   return LMVD_OK;
 }
+
+int lmvd_graphs_enable(lmvd_ctx* h, int on) {
+  if (!h) return LMVD_ERR_INVALID_ARG;
+  Ctx& c = h->c;
+  c.graphs_on = on != 0;
+  if (!c.graphs_on) graphs_clear(c);
+  return LMVD_OK;
+}
+
+int lmvd_graph_count(const lmvd_ctx* h) { return h ? (int)h->c.graphs.size() : -1; }
 
 size_t lmvd_field_bytes(const lmvd_ctx* h, int which) {
   if (!h) return 0;

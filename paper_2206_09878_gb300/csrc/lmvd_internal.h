@@ -216,6 +216,18 @@ struct Ctx {
   // [2 + 2k, 3 + 2k] = |dz/dt^{k+1} - dz/dt^k|^2, |dz/dt^{k+1}|^2 for k < kf
   bool diag_on = false;
   double* ddiag = nullptr;
+
+  // CUDA graphs of one substage (lmvd_graphs_enable), one per launch pattern (see graph_key in api.cu)
+  static constexpr int GRAPH_KEY = 23;
+  struct SubstageGraph {
+    const void* key[GRAPH_KEY];
+    cudaGraphExec_t exec;
+    long long launches;  // kernels in the graph, and their per-class accounting
+    long long n[KC_COUNT];
+    double flops[KC_COUNT], bytes[KC_COUNT];
+  };
+  bool graphs_on = true;
+  std::vector<SubstageGraph> graphs;
 };
 
 // one substage (api.cu); with a tape the physical fields the adjoint needs are kept

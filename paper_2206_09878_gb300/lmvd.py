@@ -73,6 +73,8 @@ def _load():
         "lmvd_device_bytes": (S, [P]),
         "lmvd_diagnostics_enable": (I, [P, I]),
         "lmvd_diagnostics": (I, [P, ctypes.POINTER(ctypes.c_double), I]),
+        "lmvd_graphs_enable": (I, [P, I]),
+        "lmvd_graph_count": (I, [P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -90,7 +92,7 @@ EXPORTED = ("lmvd_default_config", "lmvd_create", "lmvd_destroy", "lmvd_set_stat
             "lmvd_profile_read", "lmvd_kernel_class_name", "lmvd_kernel_launches", "lmvd_inverse_transform",
             "lmvd_forward_transform", "lmvd_inverse_transform_noalloc", "lmvd_state_bytes",
             "lmvd_adjoint_substage", "lmvd_adjoint_startup", "lmvd_device_bytes", "lmvd_diagnostics_enable",
-            "lmvd_diagnostics")
+            "lmvd_diagnostics", "lmvd_graphs_enable", "lmvd_graph_count")
 LMVD_KERNEL_CLASSES = 13
 
 
@@ -220,6 +222,14 @@ def lmvd_state_bytes(h):
 def lmvd_adjoint_substage(h, state_bar_out, history_bar_out, state_bar_in, history_bar_in):
     _check(_lib.lmvd_adjoint_substage(h, _ptr(state_bar_out), _ptr(history_bar_out), _ptr(state_bar_in),
                                       _ptr(history_bar_in)), "lmvd_adjoint_substage")
+
+
+def lmvd_graphs_enable(h, on=True):
+    _check(_lib.lmvd_graphs_enable(h, 1 if on else 0), "lmvd_graphs_enable")
+
+
+def lmvd_graph_count(h):
+    return int(_lib.lmvd_graph_count(h))
 
 
 def lmvd_diagnostics_enable(h, on=True):
