@@ -71,7 +71,7 @@ struct Fields10R {
 // ------------------------------------------------------------------ elementwise helpers
 // f[o] *= (kx == 0 ? s0 : s1); Nyquist slots set to zero. blockIdx.y selects the field.
 __global__ void k_wscale(Grid g, FieldsW10 f, double s0, double s1) {
-  cd* x = f.p[blockIdx.y];
+  cd* x = pick(f.p, (int)blockIdx.y);
   const size_t n = (size_t)g.ny * g.M;
   for (size_t o = blockIdx.x * (size_t)blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x) {
     const int m = (int)(o % g.M);

@@ -190,7 +190,7 @@ __global__ void __launch_bounds__(256, 3) k_fft_z_inv(FFTPlan pl, Grid g, Fields
   const int bt = threadIdx.x / pl.tpt, tt = threadIdx.x - bt * pl.tpt;
   for (int idx = threadIdx.x; idx < batch * ld; idx += blockDim.x) a[idx] = F::zero();
   __syncthreads();
-  const cd* src = in.p[f] + (size_t)j * g.M;
+  const cd* src = pick(in.p, f) + (size_t)j * g.M;
   for (int idx = threadIdx.x; idx < nz * batch; idx += blockDim.x) {
     const int jz = idx / batch, bb = idx - jz * batch, kx = kx0 + bb;
     if (kx < h && jz != nz / 2) {
@@ -238,7 +238,7 @@ __global__ void __launch_bounds__(256, 3) k_fft_x_inv(FFTPlan pl, Grid g, const 
   __syncthreads();
   fft_inplace<C, 1, EPT>(a + bt * ld, pl, tt, pl.tpt);
   const C* res = a;
-  R* dst = reinterpret_cast<R*>(out.p[f]) + (size_t)j * g.P;
+  R* dst = reinterpret_cast<R*>(pick(out.p, f)) + (size_t)j * g.P;
   for (int idx = threadIdx.x; idx < batch * px; idx += blockDim.x) {
     const int bb = idx / px, x = idx - bb * px;
     const int za = 2 * (pr0 + bb), zb = za + 1;
@@ -259,7 +259,7 @@ __global__ void __launch_bounds__(256, 3) k_fft_x_fwd(FFTPlan pl, Grid g, Fields
   const int batch = pl.batch, ld = pl.n + 1, px = g.px, pz = g.pz, h = g.nx / 2;
   const int pr0 = blockIdx.x * batch, j = blockIdx.y, f = blockIdx.z;
   const int bt = threadIdx.x / pl.tpt, tt = threadIdx.x - bt * pl.tpt;
-  const R* src = reinterpret_cast<const R*>(in.p[f]) + (size_t)j * g.P;
+  const R* src = reinterpret_cast<const R*>(pick(in.p, f)) + (size_t)j * g.P;
   for (int idx = threadIdx.x; idx < batch * px; idx += blockDim.x) {
     const int bb = idx / px, x = idx - bb * px;
     const int za = 2 * (pr0 + bb), zb = za + 1;
@@ -302,7 +302,7 @@ __global__ void __launch_bounds__(256, 3) k_fft_z_fwd(FFTPlan pl, Grid g, const 
   __syncthreads();
   fft_inplace<C, -1, EPT>(a + bt * ld, pl, tt, pl.tpt);
   const C* res = a;
-  cd* dst = out.p[f] + (size_t)j * g.M;
+  cd* dst = pick(out.p, f) + (size_t)j * g.M;
   for (int idx = threadIdx.x; idx < nz * batch; idx += blockDim.x) {
     const int jz = idx / batch, bb = idx - jz * batch, kx = kx0 + bb;
     if (kx > h) continue;

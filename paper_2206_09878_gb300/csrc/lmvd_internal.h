@@ -67,6 +67,17 @@ struct Grid {
   double lx, lz;
 };
 
+// Entry f of a table passed by value as a kernel parameter. A runtime index into the parameter space makes
+// every thread copy the whole table to its local memory first; a chain of selects over the entries (each a
+// constant-bank operand) does not.
+template <class T, int N>
+__device__ __forceinline__ T pick(const T (&tab)[N], int f) {
+  T r = tab[0];
+#pragma unroll
+  for (int q = 1; q < N; ++q) r = (f == q) ? tab[q] : r;
+  return r;
+}
+
 __device__ inline bool is_nyquist(const Grid& g, int m) {
   int kx = m % g.nxh, jz = m / g.nxh;
   return kx == g.nx / 2 || jz == g.nz / 2;

@@ -337,7 +337,7 @@ __global__ void k_update_m2_rhs(Grid g, DBand Ss0, DBand Ss2, UpdateArgs a) {
 // Sets bit 0 of *flag if array blockIdx.y of the job list holds a non-finite double (inf or nan: all
 // exponent bits set). Integer tests on the bit pattern keep this off the FP64 pipe; one atomic per warp.
 __global__ void k_check_finite(CheckJobs jobs, unsigned* flag) {
-  const CheckJob& jb = jobs.j[blockIdx.y];
+  const CheckJob jb = pick(jobs.j, (int)blockIdx.y);
   bool bad = false;
   for (size_t o = blockIdx.x * (size_t)blockDim.x + threadIdx.x; o < jb.n; o += (size_t)gridDim.x * blockDim.x)
     bad |= (__double_as_longlong(jb.p[o]) & 0x7FF0000000000000ll) == 0x7FF0000000000000ll;
