@@ -128,6 +128,14 @@ __device__ __forceinline__ df dadd(df a, df b) {
   fast_two_sum(s, e, r, rl);
   return df{r, rl};
 }
+// a + b without the final renormalisation: hi + lo is the sum to the same accuracy, but lo may exceed
+// ulp(hi) / 2. For intermediates that only feed another dadd (its TwoSum of the high parts is exact for
+// any operands and it renormalises its result).
+__device__ __forceinline__ df dadd_lazy(df a, df b) {
+  float s, e;
+  two_sum(a.hi, b.hi, s, e);
+  return df{s, __fadd_rn(e, __fadd_rn(a.lo, b.lo))};
+}
 __device__ __forceinline__ df dneg(df a) { return df{-a.hi, -a.lo}; }
 __device__ __forceinline__ df dsub(df a, df b) { return dadd(a, dneg(b)); }
 __device__ __forceinline__ df dmul(df a, df b) {
@@ -156,13 +164,34 @@ __device__ __forceinline__ df ddot2(df a, df b, df c, df d) {
   fast_two_sum(s, t, r, rl);
   return df{r, rl};
 }
+// a * b + c * d without the final renormalisation (see dadd_lazy)
+__device__ __forceinline__ df ddot2_lazy(df a, df b, df c, df d) {
+  const float p1 = __fmul_rn(a.hi, b.hi), e1 = __fmaf_rn(a.hi, b.hi, -p1);
+  const float p2 = __fmul_rn(c.hi, d.hi), e2 = __fmaf_rn(c.hi, d.hi, -p2);
+  float s, e3;
+  two_sum(p1, p2, s, e3);
+  float t = __fadd_rn(__fadd_rn(e1, e2), e3);
+  t = __fmaf_rn(a.hi, b.lo, t);
+  t = __fmaf_rn(a.lo, b.hi, t);
+  t = __fmaf_rn(c.hi, d.lo, t);
+  t = __fmaf_rn(c.lo, d.hi, t);
+  return df{s, t};
+}
+
 // complex helpers
 __device__ __forceinline__ cdf cadd(cdf a, cdf b) { return cdf{dadd(a.re, b.re), dadd(a.im, b.im)}; }
 __device__ __forceinline__ cdf csub(cdf a, cdf b) { return cdf{dsub(a.re, b.re), dsub(a.im, b.im)}; }
+__device__ __forceinline__ cdf cadd_lazy(cdf a, cdf b) { return cdf{dadd_lazy(a.re, b.re), dadd_lazy(a.im, b.im)}; }
+__device__ __forceinline__ cdf csub_lazy(cdf a, cdf b) {
+  return cdf{dadd_lazy(a.re, dneg(b.re)), dadd_lazy(a.im, dneg(b.im))};
+}
 __device__ __forceinline__ cdf ctimes_i(cdf a) { return cdf{dneg(a.im), a.re}; }
 __device__ __forceinline__ cdf cconj(cdf a) { return cdf{a.re, dneg(a.im)}; }
 __device__ __forceinline__ cdf cmulw(cdf v, df wr, df wi) {  // v * (wr + i wi)
   return cdf{ddot2(v.re, wr, dneg(v.im), wi), ddot2(v.re, wi, v.im, wr)};
+}
+__device__ __forceinline__ cdf cmulw_lazy(cdf v, df wr, df wi) {  // the same, not renormalised
+  return cdf{ddot2_lazy(v.re, wr, dneg(v.im), wi), ddot2_lazy(v.re, wi, v.im, wr)};
 }
 
 }  // namespace lmvd

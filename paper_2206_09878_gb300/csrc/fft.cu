@@ -49,6 +49,8 @@ struct FT<cd> {
   __device__ static cd zero() { return mk(0, 0); }
   __device__ static cd add(cd a, cd b) { return a + b; }
   __device__ static cd sub(cd a, cd b) { return a - b; }
+  __device__ static cd add_lazy(cd a, cd b) { return a + b; }
+  __device__ static cd sub_lazy(cd a, cd b) { return a - b; }
   __device__ static cd ti(cd a) { return times_i(a); }
   __device__ static cd neg(cd a) { return cd{-a.re, -a.im}; }
   __device__ static cd cj(cd a) { return conj(a); }
@@ -76,6 +78,9 @@ struct FT<cdf> {
   __device__ static cdf zero() { return cdf{df{0.f, 0.f}, df{0.f, 0.f}}; }
   __device__ static cdf add(cdf a, cdf b) { return cadd(a, b); }
   __device__ static cdf sub(cdf a, cdf b) { return csub(a, b); }
+  // intermediates of a butterfly that feed only add / sub: not renormalised
+  __device__ static cdf add_lazy(cdf a, cdf b) { return cadd_lazy(a, b); }
+  __device__ static cdf sub_lazy(cdf a, cdf b) { return csub_lazy(a, b); }
   __device__ static cdf ti(cdf a) { return ctimes_i(a); }
   __device__ static cdf neg(cdf a) { return cdf{dneg(a.re), dneg(a.im)}; }
   __device__ static cdf cj(cdf a) { return cconj(a); }
@@ -85,7 +90,7 @@ struct FT<cdf> {
     const float4 w = p.twf[idx];
     const df wr{w.x, w.y};
     const df wi = SIGN > 0 ? df{w.z, w.w} : df{-w.z, -w.w};
-    return cmulw(v, wr, wi);
+    return cmulw_lazy(v, wr, wi);  // feeds only the butterfly's add / sub
   }
   template <int SIGN>
   __device__ static cdf mul_s3(cdf v, const FFTPlan& p) {
@@ -131,17 +136,18 @@ __device__ __forceinline__ void fft_stage(C* x, const FFTPlan& pl, int L, int tt
       for (int q = 1; q < R; ++q) v[j][q] = F::template mulw<SIGN>(v[j][q], pl, q * k * tws);
     }
     if (R == 4) {
-      const C t0 = F::add(v[j][0], v[j][2]), t1 = F::sub(v[j][0], v[j][2]), t2 = F::add(v[j][1], v[j][3]);
-      const C d3 = F::ti(F::sub(v[j][1], v[j][3]));
+      const C t0 = F::add_lazy(v[j][0], v[j][2]), t1 = F::sub_lazy(v[j][0], v[j][2]);
+      const C t2 = F::add_lazy(v[j][1], v[j][3]);
+      const C d3 = F::ti(F::sub_lazy(v[j][1], v[j][3]));
       const C t3 = SIGN > 0 ? d3 : F::neg(d3);  // (SIGN i) (v1 - v3)
       x[base] = F::add(t0, t2);
       x[base + L] = F::add(t1, t3);
       x[base + 2 * L] = F::sub(t0, t2);
       x[base + 3 * L] = F::sub(t1, t3);
     } else if (R == 3) {
-      const C t1 = F::add(v[j][1], v[j][2]);
-      const C m = F::sub(v[j][0], F::half(t1));
-      const C u = F::ti(F::template mul_s3<SIGN>(F::sub(v[j][1], v[j][2]), pl));
+      const C t1 = F::add_lazy(v[j][1], v[j][2]);
+      const C m = F::sub_lazy(v[j][0], F::half(t1));
+      const C u = F::ti(F::template mul_s3<SIGN>(F::sub_lazy(v[j][1], v[j][2]), pl));
       x[base] = F::add(v[j][0], t1);
       x[base + L] = F::add(m, u);
       x[base + 2 * L] = F::sub(m, u);
