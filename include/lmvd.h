@@ -199,6 +199,20 @@ int lmvd_forward_transform(lmvd_ctx* ctx, const double* phys, void* spec, int nf
 int lmvd_inverse_transform_noalloc(int nx, int ny, int nz, const void* spec, double* phys, int nfields,
                                    void* cuda_stream);
 
+/* Self-test of the precision path's conversions (precision = 1; no paper counterpart). The spectral
+ * ends of its transforms split each FP64 value into a double-float pair and round pairs back, with
+ * integer operations only; this runs the same device code on caller arrays:
+ *   (hi[i], lo[i]) = split of x[i]: hi the top 24 significand bits of x (truncated), lo the rest rounded
+ *     to a float, renormalised (|lo| <= ulp(hi) / 2, |hi + lo - x| <= 2^-48 |x| for |x| >= 2^-102;
+ *     smaller magnitudes lose lo gradually and become signed zeros below 2^-126; |x| >= 2^128 gives a
+ *     signed infinity, nan a nan);
+ *   sum[i] = pair_hi[i] + pair_lo[i] rounded to a double (exact when representable; otherwise the
+ *     bits of pair_lo below the double's last place rounded to nearest); inf and nan keep their value.
+ * All arrays are caller-owned device memory of n entries; asynchronous on cuda_stream.
+ * Errors: INVALID_ARG (NULL pointer with n > 0), CUDA. */
+int lmvd_df64_convert(const double* x, float* hi, float* lo, const float* pair_hi, const float* pair_lo,
+                      double* sum, size_t n, void* cuda_stream);
+
 /* Adjoint of one substage (the differentiation path; the paper's method is differentiated, the paper
  * itself has no adjoint). Let x = (state, history) be the context's current state and history and
  * y = (state', history') what lmvd_advance_substage would produce from it. Given ybar, this computes

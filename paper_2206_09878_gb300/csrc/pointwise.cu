@@ -3,6 +3,8 @@
 // Paper Sec. 2.1 (R_z, L), Sec. 4.3 (applying L: rho_t = f'(z) dz/dt, then -(1/rho) grad z . m^c),
 // Eq. om / phi (C_ij = -rho u_i u_j), Sec. 5 (binary-mixing EOS rho = rl rh / (rh - (rh - rl) z)).
 // 1/rho is linear in z, so the EOS needs one division per point (rho itself, used by gravity).
+#include <algorithm>
+
 #include "ykernels.h"
 
 namespace lmvd {
@@ -131,3 +133,26 @@ __global__ void k_products_p2_df(size_t n, const double* md1, const double* md2,
 }
 
 }  // namespace lmvd
+
+// ------------------------------------------------------------------ conversion self-test
+namespace lmvd {
+__global__ void k_df64_convert(size_t n, const double* x, float* hi, float* lo, const float* pair_hi,
+                               const float* pair_lo, double* sum) {
+  for (size_t o = blockIdx.x * (size_t)blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x) {
+    const df d = df_from_double_int(x[o]);
+    hi[o] = d.hi;
+    lo[o] = d.lo;
+    sum[o] = df_to_double_int(df{pair_hi[o], pair_lo[o]});
+  }
+}
+}  // namespace lmvd
+
+extern "C" int lmvd_df64_convert(const double* x, float* hi, float* lo, const float* pair_hi, const float* pair_lo,
+                                 double* sum, size_t n, void* cuda_stream) {
+  using namespace lmvd;
+  if (n == 0) return LMVD_OK;
+  if (!x || !hi || !lo || !pair_hi || !pair_lo || !sum) return LMVD_ERR_INVALID_ARG;
+  const size_t blocks = std::min<size_t>((n + 255) / 256, 4096);
+  k_df64_convert<<<(unsigned)blocks, 256, 0, (cudaStream_t)cuda_stream>>>(n, x, hi, lo, pair_hi, pair_lo, sum);
+  return cudaGetLastError() == cudaSuccess ? LMVD_OK : LMVD_ERR_CUDA;
+}

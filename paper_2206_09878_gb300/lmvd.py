@@ -75,6 +75,7 @@ def _load():
         "lmvd_diagnostics": (I, [P, ctypes.POINTER(ctypes.c_double), I]),
         "lmvd_graphs_enable": (I, [P, I]),
         "lmvd_graph_count": (I, [P]),
+        "lmvd_df64_convert": (I, [P, P, P, P, P, P, S, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -92,7 +93,7 @@ EXPORTED = ("lmvd_default_config", "lmvd_create", "lmvd_destroy", "lmvd_set_stat
             "lmvd_profile_read", "lmvd_kernel_class_name", "lmvd_kernel_launches", "lmvd_inverse_transform",
             "lmvd_forward_transform", "lmvd_inverse_transform_noalloc", "lmvd_state_bytes",
             "lmvd_adjoint_substage", "lmvd_adjoint_startup", "lmvd_device_bytes", "lmvd_diagnostics_enable",
-            "lmvd_diagnostics", "lmvd_graphs_enable", "lmvd_graph_count")
+            "lmvd_diagnostics", "lmvd_graphs_enable", "lmvd_graph_count", "lmvd_df64_convert")
 LMVD_KERNEL_CLASSES = 13
 
 
@@ -226,6 +227,14 @@ def lmvd_adjoint_substage(h, state_bar_out, history_bar_out, state_bar_in, histo
 
 def lmvd_graphs_enable(h, on=True):
     _check(_lib.lmvd_graphs_enable(h, 1 if on else 0), "lmvd_graphs_enable")
+
+
+def lmvd_df64_convert(x, hi, lo, pair_hi, pair_lo, out_sum, stream=None):
+    """Device conversions of the precision path on caller tensors (see lmvd.h)."""
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    _check(_lib.lmvd_df64_convert(_ptr(x), _ptr(hi), _ptr(lo), _ptr(pair_hi), _ptr(pair_lo), _ptr(out_sum),
+                                  int(x.numel()), ctypes.c_void_p(stream.cuda_stream)), "lmvd_df64_convert")
 
 
 def lmvd_graph_count(h):

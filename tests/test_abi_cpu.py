@@ -21,7 +21,7 @@ def lib():
 
 def declared():
     src = open(os.path.join(ROOT, "include", "lmvd.h")).read()
-    return sorted(set(re.findall(r"\b(lmvd_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(lmvd_[a-z0-9_]+)\s*\(", src)))
 
 
 def test_every_declared_symbol_is_exported(lib):
