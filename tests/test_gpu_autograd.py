@@ -44,7 +44,7 @@ def run(ctx, lay, state, hist, every, grad=True):
     loss = loss_of(lay, out_s)
     if grad:
         loss.backward()
-        return float(loss), s.grad.clone(), h.grad.clone()
+        return float(loss.detach()), s.grad.clone(), h.grad.clone()
     return float(loss)
 
 
