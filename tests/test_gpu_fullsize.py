@@ -168,13 +168,12 @@ def test_double_float_path_agrees_with_fp64_full_size(L, W, run0):
         assert rel < 1e-12, (k, rel)
 
 
+@pytest.mark.parametrize("W", ["rt256"], indirect=True)
 def test_twenty_rk_steps_256(L, ops, W):
     """20 RK steps (40 substages) at 256 x 257 x 256, dt = 2e-4, density ratio 25.7: the state stays finite
     and Hermitian, m^c of the last substage conserves mass exactly, and the last substage (stage ', al = 1,
     be = -1/2) updates Omega2 and m2^d of sampled modes as the oracle's matrices do from the GPU's state,
     RHS and previous RHS (from the history)."""
-    if W != "rt256":
-        pytest.skip("the 20-step run is the 256 x 257 x 256 configuration")
     from oracle import banded
     from oracle.lmvd import _ax0
     before, f, after = _run(L, W, 0, 40, history=True)
