@@ -103,7 +103,8 @@ int lmvd_default_config(lmvd_config* cfg, int nx, int ny, int nz);
  * cuda_stream: a cudaStream_t (NULL = legacy default stream) on which every later call runs.
  * *out receives a context owned by the caller until lmvd_destroy. Synchronous.
  * Errors: INVALID_ARG (NULL pointers, bad sizes), UNSUPPORTED (grid sizes the transforms do not
- * handle), OOM (device allocation failed), CUDA (any other CUDA failure). */
+ * handle: 3nx/2 and 3nz/2 must have no prime factors but 2 and 3, 3nx/2 <= 1536, 3nz/2 <= 3072),
+ * OOM (device allocation failed), CUDA (any other CUDA failure). */
 int lmvd_create(const lmvd_config* cfg, void* cuda_stream, lmvd_ctx** out);
 
 /* Release all device memory of the context. NULL is ignored. */
@@ -195,7 +196,8 @@ int lmvd_forward_transform(lmvd_ctx* ctx, const double* phys, void* spec, int nf
  * stream capture. All calls on a device share the array and leave their contents in it; calls whose
  * GPU work overlaps (different streams or host threads) race, so order them on one stream.
  * Errors: INVALID_ARG (NULL pointer, odd or too small nx/nz, nfields < 0, grid too large for the static
- * array), UNSUPPORTED (3nx/2 or 3nz/2 with prime factors other than 2 and 3), CUDA. */
+ * array), UNSUPPORTED (3nx/2 or 3nz/2 with prime factors other than 2 and 3, or above the limits of
+ * lmvd_create), CUDA. */
 int lmvd_inverse_transform_noalloc(int nx, int ny, int nz, const void* spec, double* phys, int nfields,
                                    void* cuda_stream);
 
