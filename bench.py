@@ -44,7 +44,7 @@ DF64_EQ_PEAK_TFLOPS = 152 * 128 * 2.07e9 / 10 / 1e12
 #   (0, fft_x_inverse, 768): 2025.8 MB over 101376 units (512 x 33 x 512, 8 fields) = 19983 B per unit,
 #   (1, fft_x_inverse, 768): 2031.4 MB over the same units = 20038 B per unit,
 #   against 2 (16 nx/2 + 8 px) = 20480 algorithmic bytes.
-NCU_DRAM_BYTES_PER_UNIT = {(0, "fft_x_inverse", 768): 19983.0, (1, "fft_x_inverse", 768): 20038.0}
+NCU_DRAM_BYTES_PER_UNIT = {(0, "fft_x_inverse", 768): 18550.0, (1, "fft_x_inverse", 768): 18422.0}
 CPU_SAMPLE_N = 128
 
 
