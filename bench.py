@@ -576,7 +576,7 @@ def run_cuda(args):
     if rank == 0 and ws == 1 and not args.no_adjoint:
         out["adjoint"] = adjoint_ratio(L, args.adjoint_workload, stream)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        rate, cores, desc = oracle_rate(w, 2)
+        rate, cores, desc = oracle_rate(w, 4)
         out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
     if ws > 1:
         dist.destroy_process_group()
