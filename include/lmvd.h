@@ -117,7 +117,9 @@ void lmvd_destroy(lmvd_ctx* ctx);
  * applications of the fixed point of Eq. dz_fixedpoint_stageone from dz/dt = 0, then the z history
  * of Eq. dzdt_guesses is back-filled with Taylor steps z - j dt/2 dz/dt, j = 1, 2, 3 (the paper
  * leaves start-up open). Nyquist slots and the k = 0 slot of Omega2 and m2^d are zeroed.
- * Errors: INVALID_ARG (NULL ctx or state pointer), CUDA. */
+ * Asynchronous on the context's stream, except that with a history blob its substage counter is read
+ * to the host in stream order (the stream is synchronised once).
+ * Errors: INVALID_ARG (NULL ctx or state pointer, negative counter), CUDA. */
 int lmvd_set_state(lmvd_ctx* ctx, const void* z_hat, const void* omega2_hat, const void* m2d_hat,
                    const double* mean_m1, const double* mean_m3, const void* history);
 

@@ -886,7 +886,11 @@ int lmvd_set_state(lmvd_ctx* h, const void* z, const void* om, const void* m2, c
   }
   const char* hb = (const char*)history;
   long long s = 0;
-  if (cudaMemcpy(&s, hb, sizeof(s), cudaMemcpyDefault) != cudaSuccess) return latch(c, LMVD_ERR_CUDA);
+  // the counter is read in the context's stream order (the caller may have written the blob on that
+  // stream an instant ago; a plain cudaMemcpy runs on the legacy stream, which does not wait for it)
+  if (cudaMemcpyAsync(&s, hb, sizeof(s), cudaMemcpyDefault, c.stream) != cudaSuccess ||
+      cudaStreamSynchronize(c.stream) != cudaSuccess)
+    return latch(c, LMVD_ERR_CUDA);
   if (s < 0) return LMVD_ERR_INVALID_ARG;
   size_t off = 16;
   for (int q = 0; q < 3 && !e; ++q, off += S) e = copy_in(c, c.zh[q], hb + off, S);

@@ -68,3 +68,27 @@ def test_checkpoint_spacing_does_not_change_gradient(setup):
     _, g2, h2 = run(ctx, lay, state, hist, every=2)
     _, g6, h6 = run(ctx, lay, state, hist, every=6)
     assert torch.equal(g2, g6) and torch.equal(h2, h6)
+
+
+def test_gradient_with_graph_replay_on_a_side_stream(setup):
+    """The same gradient from a context on a side stream, where the forward substages (the checkpointed
+    run and the segment recomputations) replay CUDA graphs and only the adjoint's recording runs eagerly:
+    bit for bit the gradient of the legacy-stream context, which launches everything eagerly. It also
+    checks that lmvd_set_state reads the counter of a history blob written on that stream a moment before
+    in stream order (a read on the legacy stream saw a stale counter and ran the wrong RK stage)."""
+    from _pairs import make_pair
+    from paper_2206_09878_gb300 import lmvd as L
+    from paper_2206_09878_gb300.autograd import Layout
+    ctx, lay, state, hist = setup
+    _, g_ref, h_ref = run(ctx, lay, state, hist, every=2)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        _, ctx2, _, _ = make_pair(L, "rt32", u_rms=1e-2)   # created on the current (side) stream
+        lay2 = Layout(ctx2)
+        _, g2, h2 = run(ctx2, lay2, state, hist, every=2)
+        held = L.lmvd_graph_count(ctx2.h)
+        torch.cuda.synchronize()
+        ctx2.close()
+    assert held > 0
+    assert torch.equal(g_ref, g2) and torch.equal(h_ref, h2)
