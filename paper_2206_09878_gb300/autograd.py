@@ -48,6 +48,7 @@ def set_state(ctx, lay, state, hblob):
     """hblob None: the start-up runs (lmvd_set_state without history)."""
     u8 = state.contiguous().view(torch.uint8)
     v = {k: u8[o:o + n] for k, (o, n) in lay.off.items()}
+    ctx.wait_inputs()
     L.lmvd_set_state(ctx.h, v["z"], v["om"], v["m2"], v["mm1"], v["mm3"], hblob)
 
 
@@ -56,7 +57,9 @@ def get_state(ctx, lay, dev):
     hblob = torch.empty(lay.hist_bytes, dtype=torch.uint8, device=dev)
     u8 = state.view(torch.uint8)
     v = {k: u8[o:o + n] for k, (o, n) in lay.off.items()}
+    ctx.wait_inputs()
     L.lmvd_get_state(ctx.h, v["z"], v["om"], v["m2"], v["mm1"], v["mm3"], hblob)
+    ctx.publish()
     return state, hblob
 
 
@@ -103,6 +106,7 @@ class Substages(torch.autograd.Function):
                 set_state(ctx, lay, xs, xh)
                 xbs = torch.empty_like(ys)
                 xbh = torch.empty(lay.hist_bytes, dtype=torch.uint8, device=dev)
+                ctx.wait_inputs()
                 L.lmvd_adjoint_substage(ctx.h, ys.view(torch.uint8), yh, xbs.view(torch.uint8), xbh)
                 ys, yh = xbs, xbh
         ctx.synchronize()
@@ -129,5 +133,6 @@ class Startup(torch.autograd.Function):
                           if g_hist is None else g_hist, 0)
         set_state(ctx, lay, x, hb)   # the state x; lmvd_adjoint_startup re-runs the start-up from it
         xb = torch.empty_like(x)
+        ctx.wait_inputs()
         L.lmvd_adjoint_startup(ctx.h, ys.view(torch.uint8), yh, xb.view(torch.uint8))
         return xb, None

@@ -271,7 +271,8 @@ class Context:
     def __init__(self, cfg, device="cuda", stream=None):
         self.cfg = cfg
         self.device = torch.device(device)
-        self.h = lmvd_create(cfg, stream)
+        self.stream = torch.cuda.current_stream() if stream is None else stream
+        self.h = lmvd_create(cfg, self.stream)
         nxh = cfg.nx // 2 + 1
         self.shape = (cfg.ny, cfg.nz, nxh)
         self.shape_m2 = (cfg.ny + 1, cfg.nz, nxh)
@@ -287,12 +288,28 @@ class Context:
                     mm1=torch.zeros(self.cfg.ny, dtype=torch.float64, **kw),
                     mm3=torch.zeros(self.cfg.ny, dtype=torch.float64, **kw))
 
+    # Stream order between torch and the library: tensors handed to the library were produced on torch's
+    # current stream, so the context's stream waits for it first (wait_inputs); tensors the library writes
+    # are read on torch's current stream, which waits for the context's stream afterwards (publish).
+    def wait_inputs(self):
+        cur = torch.cuda.current_stream()
+        if cur != self.stream:
+            self.stream.wait_stream(cur)
+
+    def publish(self):
+        cur = torch.cuda.current_stream()
+        if cur != self.stream:
+            cur.wait_stream(self.stream)
+
     def set_state(self, st, history=None):
+        self.wait_inputs()
         lmvd_set_state(self.h, st["z"], st["om"], st["m2"], st["mm1"], st["mm3"], history)
 
     def get_state(self, out=None, history=None):
         out = self.empty_state() if out is None else out
+        self.wait_inputs()
         lmvd_get_state(self.h, out["z"], out["om"], out["m2"], out["mm1"], out["mm3"], history)
+        self.publish()
         return out
 
     def history_buffer(self, device=None):
@@ -306,7 +323,9 @@ class Context:
         else:
             rows = nbytes // (16 * self.cfg.nz * (self.cfg.nx // 2 + 1))
             out = torch.zeros((rows, self.cfg.nz, self.cfg.nx // 2 + 1), dtype=torch.complex128, device=self.device)
+        self.wait_inputs()
         lmvd_get_field(self.h, which, out)
+        self.publish()
         return out
 
     def advance_substage(self):
