@@ -148,7 +148,8 @@ int lmvd_step(lmvd_ctx* ctx, int nsteps);
  * z history cycles through five buffers, the other fields through two). Results are those of the
  * eager launches (same kernels, same arguments, same order). Substages run eagerly while per-launch
  * profiling is on, inside the adjoint's recording, on the legacy default stream (ctx created with a
- * NULL stream), or after a capture was refused. Off: eager launches, the graphs are released.
+ * NULL stream), while the caller is capturing the stream (the launches then go into the caller's
+ * graph), or after a capture was refused. Off: eager launches, the graphs are released.
  * Errors: INVALID_ARG (NULL). */
 int lmvd_graphs_enable(lmvd_ctx* ctx, int on);
 

@@ -659,7 +659,10 @@ Ctx::SubstageGraph* graph_find(Ctx& c) {
 int advance_impl(Ctx& c, const Tape* tape) {
   // the graph path: not with a tape (adjoint recording), not while profiling (its events time each
   // launch), not on the legacy default stream (it cannot be captured)
-  if (c.graphs_on && !tape && !c.prof.on && c.stream) {
+  // nor while the caller is capturing the stream into a graph of its own (the launches then go into it)
+  cudaStreamCaptureStatus capturing = cudaStreamCaptureStatusNone;
+  if (c.graphs_on && !tape && !c.prof.on && c.stream &&
+      cudaStreamIsCapturing(c.stream, &capturing) == cudaSuccess && capturing == cudaStreamCaptureStatusNone) {
     Ctx::SubstageGraph* G = graph_find(c);
     if (!G) G = graph_capture(c);
     if (G) {

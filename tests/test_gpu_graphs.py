@@ -108,3 +108,30 @@ def test_diagnostics_and_profiling_with_graphs(L):
         assert sum(p[0] for p in prof) > 0 and sum(p[1] for p in prof) > 0
         assert L._lib.lmvd_synchronize(ctx.h) == 0
         ctx.close()
+
+
+def test_substage_inside_a_callers_graph_capture(L):
+    """A caller capturing the context's stream (torch.cuda.graph) gets the substage's launches in its own
+    graph: the library does not start a capture of its own; one replay equals one eager substage."""
+    from _pairs import to_torch
+    s = torch.cuda.Stream()
+    out = {}
+    with torch.cuda.stream(s):
+        for mode in ("eager", "caller_graph"):
+            _, ctx, st = _setup(L, 0, mode != "eager")
+            ctx.set_state(to_torch(st))
+            ctx.advance_substage()
+            if mode == "eager":
+                ctx.advance_substage()
+            else:
+                torch.cuda.synchronize()
+                g = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(g, stream=s):
+                    ctx.advance_substage()
+                assert L.lmvd_graph_count(ctx.h) == 1        # only the substage before the capture
+                g.replay()
+            out[mode] = {k: v.cpu() for k, v in ctx.get_state().items()}
+            ctx.synchronize()
+            ctx.close()
+    for k in out["eager"]:
+        assert torch.equal(out["eager"][k], out["caller_graph"][k]), k
