@@ -26,7 +26,6 @@ __host__ __device__ inline df df_from_double(double x) {
   const float h = (float)x;
   return df{h, (float)(x - (double)h)};
 }
-__host__ __device__ inline double df_to_double(df a) { return (double)a.hi + (double)a.lo; }
 
 // Split of a double into hi + lo with integer operations only (no FP64 instruction): hi takes the
 // sign, exponent and the top 23 stored mantissa bits (truncation), lo the remaining 29 bits rounded
@@ -187,10 +186,8 @@ __device__ __forceinline__ cdf csub_lazy(cdf a, cdf b) {
 }
 __device__ __forceinline__ cdf ctimes_i(cdf a) { return cdf{dneg(a.im), a.re}; }
 __device__ __forceinline__ cdf cconj(cdf a) { return cdf{a.re, dneg(a.im)}; }
-__device__ __forceinline__ cdf cmulw(cdf v, df wr, df wi) {  // v * (wr + i wi)
-  return cdf{ddot2(v.re, wr, dneg(v.im), wi), ddot2(v.re, wi, v.im, wr)};
-}
-__device__ __forceinline__ cdf cmulw_lazy(cdf v, df wr, df wi) {  // the same, not renormalised
+// v * (wr + i wi), not renormalised (the twiddle products feed only a butterfly's additions)
+__device__ __forceinline__ cdf cmulw_lazy(cdf v, df wr, df wi) {
   return cdf{ddot2_lazy(v.re, wr, dneg(v.im), wi), ddot2_lazy(v.re, wi, v.im, wr)};
 }
 
