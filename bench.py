@@ -12,7 +12,7 @@ interface modes |k| <= 32, rms 2e-3, Re 5000), plain FP64.
 the library's stream around K substages with the state resident in HBM (inputs are > 100 GB, far
 larger than L2, so no flush is needed); `e2e` times the same substage through the public API with
 pinned host buffers (state + history copied in and out every substage). Under torchrun each rank
-runs an independent replica (the substage is not sharded on one-GPU machines); `value` sums the work
+runs an independent replica (the substage runs on one GPU, unsharded); `value` sums the work
 of all ranks over the slowest rank's time.
 --impl reference: the FP64 CPU oracle on the host cores, one bounded-sample substage per step.
 """
