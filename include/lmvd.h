@@ -27,7 +27,9 @@
  * gives asynchronous copies); they are read or written on the context's stream with
  * cudaMemcpyDefault and remain owned by the caller. The library owns only its own workspace.
  * Every call is asynchronous on the context's stream unless it says otherwise; a caller that
- * reads an output must synchronize that stream (or call lmvd_synchronize).
+ * reads an output must synchronize that stream (or call lmvd_synchronize). Inputs written on another
+ * stream must be ordered before the call by the caller (e.g. an event the context's stream waits on);
+ * the Python binding's Context does this for the tensors it exchanges.
  *
  * Errors: every int-returning call returns LMVD_OK (0) or a negative LMVD_ERR_* code and never
  * traps the GPU. The first error is also latched in the context (lmvd_status).
@@ -63,7 +65,8 @@ extern "C" {
  * precision   : 0 = FP64 throughout; 1 = transforms and physical-space products in double-float
  *               arithmetic on the FP32 units (pairs of floats, 48-bit significand, error-free
  *               TwoSum/TwoProd compensation), while every spectral step (collocation, m^c and m2^d
- *               solves, RHS assembly, the RK update and the state) stays FP64.
+ *               solves, RHS assembly, the RK update and the state) and the EOS (rho, 1/rho, f'(z))
+ *               stay FP64.
  * bc_mode     : boundary rows at y0 and y1. 0 = no-slip walls: Omega2 = 0, m2^d = dm2^d/dy = 0,
  *               m2^c = 0, <m1> = <m3> = 0, dz/dy = 0, <m2^c>(y1) = 0.
  *               1 = the paper's potential matching (Sec. 4.5, Eq. bc_both, md_bc) for a domain
