@@ -1,0 +1,33 @@
+"""CPU checks of the arithmetic behind bench.py's `roofline` object: the dominant class is the one with the
+most kernel time, achieved = its algorithmic flops / its summed kernel time, frac = achieved / peak of its
+arithmetic, and the DRAM traffic is the ncu bytes per unit (one complex px-point x-transform) times the
+units of the class's average launch, whose algorithmic bytes are 2 (16 nx/2 + 8 px) per unit."""
+import pytest
+
+
+def test_dominant_class_and_rates():
+    import bench
+    # (ms, launches, flops, bytes) per class, as lmvd_profile_read returns them
+    prof = {"fft_x_inverse": (200.0, 10.0, 1.5e14, 9.0e10), "eval": (50.0, 5.0, 5e13, 1e10),
+            "products": (20.0, 4.0, 1e12, 8e10)}
+    r = bench.roofline_of(prof, 400.0, 0, (512, 513, 512))
+    assert r["kernel"] == "fft_x_inverse" and r["bound"] == "alu" and r["unit"] == "TFLOP/s"
+    assert r["achieved"] == pytest.approx(1.5e14 / 0.2 / 1e12)
+    assert r["peak"] == pytest.approx(152 * 2 * 2 * 2.07e9 / 1e12)
+    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
+    assert r["launches"] == 10 and r["algorithmic_bytes_per_launch"] == pytest.approx(9.0e9)
+    assert r["achieved_hbm_gbs"] == pytest.approx(9.0e10 / 0.2 / 1e9)
+    assert r["share_of_step"] == pytest.approx(0.5)
+    units = 9.0e9 / (2.0 * (16 * 256 + 8 * 768))
+    assert r["traffic"] == pytest.approx(bench.NCU_DRAM_BYTES_PER_UNIT[(0, "fft_x_inverse", 768)] * units)
+    rd = bench.roofline_of(prof, 400.0, 1, (512, 513, 512))
+    assert rd["peak"] == pytest.approx(152 * 128 * 2.07e9 / 10 / 1e12)
+    assert rd["traffic"] == pytest.approx(bench.NCU_DRAM_BYTES_PER_UNIT[(1, "fft_x_inverse", 768)] * units)
+
+
+def test_traffic_is_null_without_a_matching_capture():
+    import bench
+    prof = {"solve_mc": (100.0, 5.0, 1e13, 5e10)}
+    assert bench.roofline_of(prof, 200.0, 0, (512, 513, 512))["traffic"] is None      # no capture of this class
+    prof = {"fft_x_inverse": (100.0, 5.0, 1e13, 5e10)}
+    assert bench.roofline_of(prof, 200.0, 0, (256, 257, 256))["traffic"] is None      # other transform length
