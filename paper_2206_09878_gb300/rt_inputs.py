@@ -119,18 +119,46 @@ def rt_state(nx, ny, nz, ratio, width, kmax, eta_rms, u_rms, seed, **_):
     return dict(z=zhat, om=om, m2=m2, mm1=np.zeros(ny), mm3=np.zeros(ny))
 
 
-# the paper's 3D single-mode Rayleigh-Taylor cases (Sec. 5): (nx, ny, nz, At, y0, y1, delta, steps)
+# The paper's case table (Table RT_casedetails, with the domains defined beside it), W = g = 1:
+# domain name -> (y0, y1, mesh); (dimension, At) -> Reynolds number, domain, dt sqrt(At) / sqrt(W/g).
+# The last 3D row prints the domain V^{2D,2}; as a 3D case it is read as V^{3D,2}.
+PAPER_DOMAINS = {"2D,1": (-2.0, 2.0, (128, 512)), "2D,2": (-3.5, 3.5, (128, 1024)),
+                 "3D,1": (-2.0, 2.0, (128, 512, 128)), "3D,2": (-3.5, 3.5, (128, 1024, 128))}
+PAPER_CASES = {
+    (2, 0.33): dict(re=3000.0, domain="2D,1", dt_scaled=2.5e-4),
+    (2, 0.5): dict(re=3000.0, domain="2D,1", dt_scaled=2.5e-4),
+    (2, 0.67): dict(re=3000.0, domain="2D,1", dt_scaled=2.5e-4),
+    (2, 0.8): dict(re=3000.0, domain="2D,1", dt_scaled=2.5e-4),
+    (2, 0.925): dict(re=3000.0, domain="2D,2", dt_scaled=1.25e-4),
+    (3, 0.33): dict(re=1024.0, domain="3D,1", dt_scaled=2.5e-4),
+    (3, 0.5): dict(re=1024.0, domain="3D,1", dt_scaled=2.5e-4),
+    (3, 0.67): dict(re=1024.0, domain="3D,2", dt_scaled=1.25e-4),
+    (3, 0.8): dict(re=1024.0, domain="3D,2", dt_scaled=6.25e-5),
+    (3, 0.925): dict(re=1024.0, domain="3D,2", dt_scaled=3.125e-5),
+}
+
+
+def paper_dt(dim, at):
+    """Time step of the paper's table for (dim, At): dt_scaled / sqrt(At). An At the table does not list
+    takes the 2.5e-4 of its low-At rows."""
+    row = PAPER_CASES.get((dim, round(float(at), 3)))
+    return float((row["dt_scaled"] if row else 2.5e-4) / np.sqrt(at))
+
+
+# the paper's 3D single-mode Rayleigh-Taylor cases (Sec. 5): (nx, ny, nz, At, y0, y1, delta, steps);
+# rtp128 and rtp128_hi are the table's V^{3D,1} and V^{3D,2} meshes, rtp32 a small V^{3D,1} case
 PAPER_RT = {
     "rtp32": dict(nx=32, ny=65, nz=32, at=0.5, y0=-2.0, y1=2.0, delta=0.0, steps=5),
     "rtp128": dict(nx=128, ny=512, nz=128, at=0.5, y0=-2.0, y1=2.0, delta=0.0, steps=10),
-    "rtp128_hi": dict(nx=128, ny=1024, nz=128, at=0.85, y0=-3.5, y1=3.5, delta=0.5, steps=10),
+    "rtp128_hi": dict(nx=128, ny=1024, nz=128, at=0.8, y0=-3.5, y1=3.5, delta=0.5, steps=10),
 }
 
 
 def paper_rt_config(nx, ny, nz, at, y0, y1, **_):
-    """Problem constants of the paper's set-up (W = g = 1, Re = 1024, Sc = 1)."""
-    return dict(nx=nx, ny=ny, nz=nz, lx=1.0, lz=1.0, y0=y0, y1=y1, re=1024.0, sc=1.0, fr=1.0, rho_h=1.0,
-                rho_l=(1.0 - at) / (1.0 + at), dt=2.5e-4 / np.sqrt(at), bc="potential")
+    """Problem constants of the paper's 3D set-up (W = g = 1, Sc = 1; Re and dt from its case table)."""
+    row = PAPER_CASES.get((3, round(float(at), 3)), dict(re=1024.0))
+    return dict(nx=nx, ny=ny, nz=nz, lx=1.0, lz=1.0, y0=y0, y1=y1, re=row["re"], sc=1.0, fr=1.0, rho_h=1.0,
+                rho_l=(1.0 - at) / (1.0 + at), dt=paper_dt(3, at), bc="potential")
 
 
 def rt_paper_state(nx, ny, nz, y0, y1, delta, eps=0.05, **_):

@@ -23,6 +23,8 @@ import time
 
 import numpy as np
 
+from .rt_inputs import paper_dt
+
 
 def goncharov(at, dim, g=1.0, wavelength=1.0):
     c = 1.0 if dim == 3 else 3.0
@@ -115,7 +117,7 @@ def run(dim=3, at=0.5, nx=64, ny=257, nz=None, y0=-2.0, y1=2.0, delta=0.0, re=No
     from . import lmvd as L
     nz = (nx if dim == 3 else 4) if nz is None else nz
     re = (1024.0 if dim == 3 else 3000.0) if re is None else re
-    dt = 2.5e-4 / math.sqrt(at)
+    dt = paper_dt(dim, at)
     cfg = L.lmvd_default_config(nx, ny, nz, lx=1.0, lz=1.0, y0=y0, y1=y1, re=re, sc=1.0, fr=1.0, rho_heavy=1.0,
                                 rho_light=(1 - at) / (1 + at), dt=dt, bc_mode=1, precision=precision)
     torch.cuda.set_device(device)
