@@ -63,7 +63,49 @@ def test_invalid_configs_rejected_without_gpu(lib, bad):
 
 
 def test_null_arguments(lib):
-    assert lib._lib.lmvd_create(None, None, None) == -1
-    assert lib._lib.lmvd_advance_substage(None) == -1
-    assert lib._lib.lmvd_history_bytes(None) == 0
+    L = lib._lib
+    assert L.lmvd_create(None, None, None) == -1
+    assert L.lmvd_advance_substage(None) == -1
+    assert L.lmvd_step(None, 1) == -1
+    assert L.lmvd_history_bytes(None) == 0
+    assert L.lmvd_state_bytes(None) == 0
+    assert L.lmvd_device_bytes(None) == 0
+    assert L.lmvd_field_bytes(None, 0) == 0
+    assert L.lmvd_substage_index(None) == -1
+    assert L.lmvd_status(None) == -1
+    assert L.lmvd_synchronize(None) == -1
+    assert L.lmvd_kernel_launches(None) == -1
+    assert L.lmvd_profile_enable(None, 1) == -1
+    assert L.lmvd_diagnostics_enable(None, 1) == -1
+    assert L.lmvd_graphs_enable(None, 1) == -1
+    assert L.lmvd_graph_count(None) == -1
+    assert L.lmvd_set_state(None, None, None, None, None, None, None) == -1
+    assert L.lmvd_adjoint_substage(None, None, None, None, None) == -1
+    assert L.lmvd_adjoint_startup(None, None, None, None) == -1
+    assert L.lmvd_inverse_transform(None, None, None, 1) == -1
+    assert L.lmvd_forward_transform(None, None, None, 1) == -1
     assert lib.lmvd_strerror(-3) == "device out of memory"
+
+
+def test_error_strings_and_class_names(lib):
+    msgs = [lib.lmvd_strerror(c) for c in range(0, -7, -1)]
+    assert msgs[0] == "ok" and len(set(msgs)) == 7 and "unknown" not in " ".join(msgs)
+    assert lib.lmvd_strerror(-99) == "unknown error"
+    names = [lib.lmvd_kernel_class_name(c) for c in range(lib.LMVD_KERNEL_CLASSES)]
+    assert len(set(names)) == lib.LMVD_KERNEL_CLASSES and "unknown" not in names
+    assert names[:4] == ["fft_z_inverse", "fft_x_inverse", "fft_x_forward", "fft_z_forward"]
+    assert lib.lmvd_kernel_class_name(lib.LMVD_KERNEL_CLASSES) == "unknown"
+
+
+def test_host_side_argument_checks_without_gpu(lib):
+    """Checks that return before any CUDA call: the allocation-free transform's sizes and radices, and the
+    conversion self-test's empty and NULL cases."""
+    L = lib._lib
+    fake = ctypes.c_void_p(16)          # never dereferenced: every case below returns before device work
+    assert L.lmvd_inverse_transform_noalloc(2, 9, 8, fake, fake, 1, None) == -1       # nx < 4
+    assert L.lmvd_inverse_transform_noalloc(9, 9, 8, fake, fake, 1, None) == -1       # odd nx
+    assert L.lmvd_inverse_transform_noalloc(8, 9, 8, None, fake, 1, None) == -1       # NULL spec
+    assert L.lmvd_inverse_transform_noalloc(8, 9, 8, fake, fake, -1, None) == -1      # nfields < 0
+    assert L.lmvd_inverse_transform_noalloc(10, 9, 8, fake, fake, 1, None) == -5      # 3nx/2 = 15 = 3 * 5
+    assert L.lmvd_df64_convert(None, None, None, None, None, None, 0, None) == 0      # nothing to do
+    assert L.lmvd_df64_convert(None, None, None, None, None, None, 4, None) == -1
