@@ -109,3 +109,13 @@ def test_host_side_argument_checks_without_gpu(lib):
     assert L.lmvd_inverse_transform_noalloc(10, 9, 8, fake, fake, 1, None) == -5      # 3nx/2 = 15 = 3 * 5
     assert L.lmvd_df64_convert(None, None, None, None, None, None, 0, None) == 0      # nothing to do
     assert L.lmvd_df64_convert(None, None, None, None, None, None, 4, None) == -1
+
+
+def test_every_exported_function_has_a_ctypes_signature(lib):
+    """Pointers and sizes are 64-bit: a function without argtypes / restype would be called with C int
+    conversions. lmvd_destroy returns void (restype None by design)."""
+    for name in lib.EXPORTED:
+        fn = getattr(lib._lib, name)
+        assert fn.argtypes is not None, name
+        if name != "lmvd_destroy":
+            assert fn.restype is not None, name
