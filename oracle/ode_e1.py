@@ -30,6 +30,26 @@ def M3(md, mc):
     return C3 * md * mc ** 3
 
 
+def stage_coefficients(s, beta_n, beta_p):
+    """Guess coefficients of Eq. dzdt_guesses (dt dz/dt^0 = a0 z^s + a1 z^{s-1} + a2 z^{s-2} + a3 z^{s-3})
+    and the low-storage RK2 weights (alpha, beta) of substage s (even: stage n, odd: stage ')."""
+    if s % 2 == 0:
+        return (2.0, -(2.0 + 0.5 * beta_n), beta_n, -0.5 * beta_n), (0.5, 0.0)
+    return (4.0 + beta_p, -(5.0 + 2.0 * beta_p), beta_p, 1.0), (1.0, -0.5)
+
+
+def zdot_of_substage(s, z, hist, dt, kf, beta_n, beta_p, m1=None, m2=None):
+    """dz/dt^{s,k_f}: the guess of Eq. dzdt_guesses from z and its history hist = [z^{s-1}, z^{s-2},
+    z^{s-3}], then kf applications of the fixed point of Eq. y_k, dz/dt <- M1(z) dz/dt + M2(z)."""
+    m1 = M1 if m1 is None else m1
+    m2 = M2 if m2 is None else m2
+    a, _ = stage_coefficients(s, beta_n, beta_p)
+    g = (a[0] * z + a[1] * hist[0] + a[2] * hist[1] + a[3] * hist[2]) / dt
+    for _ in range(kf):
+        g = m1(z) * g + m2(z)
+    return g
+
+
 def run(dt, t_end, kf=4, beta_n=0.0, beta_p=-4.0, z0=0.5 + 0j, md0=0.5 + 0j):
     """Return (z, m^d) at t_end after round(t_end/dt) RK2 steps of Algorithm 1."""
     nsteps = int(round(t_end / dt))
@@ -38,15 +58,8 @@ def run(dt, t_end, kf=4, beta_n=0.0, beta_p=-4.0, z0=0.5 + 0j, md0=0.5 + 0j):
     hist = [z - 0.5 * dt * zdot, z - dt * zdot, z - 1.5 * dt * zdot]   # z^{s-1}, z^{s-2}, z^{s-3}
     zdot_prev, r_prev = zdot, 0j
     for s in range(2 * nsteps):
-        if s % 2 == 0:
-            a = (2.0, -(2.0 + 0.5 * beta_n), beta_n, -0.5 * beta_n)
-            al, be = 0.5, 0.0
-        else:
-            a = (4.0 + beta_p, -(5.0 + 2.0 * beta_p), beta_p, 1.0)
-            al, be = 1.0, -0.5
-        g = (a[0] * z + a[1] * hist[0] + a[2] * hist[1] + a[3] * hist[2]) / dt
-        for _ in range(kf):
-            g = M1(z) * g + M2(z)
+        _, (al, be) = stage_coefficients(s, beta_n, beta_p)
+        g = zdot_of_substage(s, z, hist, dt, kf, beta_n, beta_p)
         mc = g / C4                      # G^{-1}(f'(z) dz/dt) with f' = 1
         r = M3(md, mc)
         z_new = z + dt * (al * g + be * zdot_prev)
