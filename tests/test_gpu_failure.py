@@ -81,3 +81,23 @@ def test_fp_divergence_is_detected(L):
     assert d["fp_changes"][-1] >= 0.5
     assert L._lib.lmvd_synchronize(ctx.h) == FP_DIVERGED
     ctx.close()
+
+
+def test_oversized_grid_reports_oom_and_the_device_stays_usable(L):
+    """1024 x 1025 x 1024 needs ~575 GB of workspace even in the lean layout: lmvd_create allocates the
+    per-mode factors, fails the workspace allocation (a plain cudaMalloc error, no fault), releases what it
+    holds and returns LMVD_ERR_OOM; a context created afterwards runs a clean substage."""
+    import ctypes
+    import gc
+    from _pairs import make_pair, to_torch
+    gc.collect()
+    torch.cuda.empty_cache()
+    cfg = L.lmvd_default_config(1024, 1025, 1024)
+    h = ctypes.c_void_p()
+    assert L._lib.lmvd_create(ctypes.byref(cfg), None, ctypes.byref(h)) == -3     # LMVD_ERR_OOM
+    assert not h.value
+    S, ctx, st, _ = make_pair(L, "rt32")
+    ctx.set_state(to_torch(st))
+    ctx.advance_substage()
+    assert L._lib.lmvd_synchronize(ctx.h) == 0
+    ctx.close()
