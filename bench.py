@@ -72,6 +72,7 @@ def parse():
     ap.add_argument("--adjoint-workload", default="rt128")
     ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT comparison of the transforms")
     ap.add_argument("--no-graphs", action="store_true", help="skip the eager / CUDA-graph comparison")
+    ap.add_argument("--rates", action="store_true", help="print the issue rates of lmvd_rate_probe and exit")
     return ap.parse_args()
 
 
@@ -293,13 +294,27 @@ def traffic_per_launch(fp, kernel, grid, alg_bytes_per_launch):
     return per_unit * units
 
 
-def roofline_of(prof, ms_step_total, fp, grid):
-    """Dominant kernel class and its achieved algorithmic rate against the ALU peak of its arithmetic."""
+def measured_rates(L, iters=4000):
+    """Issue rates of this GPU from the library's probe (lmvd_rate_probe): FP64 FMA / add / multiply and
+    FP32 FMA, operations per second (8 independent chains per thread, 8 CTAs of 256 per SM)."""
+    names = ("fp64_fma", "fp64_add", "fp64_mul", "fp32_fma")
+    return {n: L.lmvd_rate_probe(op, iters) for op, n in enumerate(names)}
+
+
+def roofline_of(prof, ms_step_total, fp, grid, rates=None):
+    """Dominant kernel class and its achieved algorithmic rate against the ALU peak of its arithmetic: the
+    measured FMA rate (rates, from measured_rates) where given, else the figure derived from the SM count,
+    2 DFMA (FP64) or 128 FFMA (FP32) per clock per SM and the 2.07 GHz maximum clock."""
     top = max(prof, key=lambda k: prof[k][0])
     tms, tn, tfl, tby = prof[top]
     achieved = tfl / (tms / 1e3) / 1e12 if tms > 0 else None
-    if fp == 0:
+    if fp == 0 and rates:
+        peak, note = 2.0 * rates["fp64_fma"] / 1e12, "FP64 peak measured: 2 flop x the FP64 FMA rate of lmvd_rate_probe"
+    elif fp == 0:
         peak, note = FP64_PEAK_TFLOPS, "FP64 peak derived: 152 SMs x 2 DFMA/clk/SM (measured) x 2 flop x 2.07 GHz"
+    elif rates:
+        peak, note = rates["fp32_fma"] / 10.0 / 1e12, ("FP64-equivalent peak of double-float: the FP32 FMA rate of "
+                                                       "lmvd_rate_probe / 10 FP32 instructions per classic flop")
     else:
         peak, note = DF64_EQ_PEAK_TFLOPS, ("FP64-equivalent peak of double-float on the FP32 pipe: 152 SMs x 128 "
                                             "lanes x 2.07 GHz / 10 FP32 instructions per classic flop")
@@ -364,8 +379,9 @@ def adjoint_ratio(L, name, stream, reps=3):
 def cufft_comparison(L, w, stream, df_prof=None, steps=None, kf=4, reps=5):
     """Per-field time of the 3/2-rule synthesis and analysis at the bench grid: this library's FP64 passes
     (lmvd_inverse_transform / lmvd_forward_transform, 4 fields per call) and, as the comparison baseline,
-    cuFFT through torch.fft (irfft2 / rfft2 of the zero-padded field, padding outside the timed region)
-    in FP64 and FP32. The double-float per-field times come from the precision-1 run's kernel profile
+    cuFFT through torch.fft in FP64 and FP32: irfft2 / rfft2 of the zero-padded field (padding outside the
+    timed region), and the pruned pipeline (1D transforms along z over the retained columns only, then
+    along x; the padding and truncation copies timed with it). The double-float per-field times come from the precision-1 run's kernel profile
     (8 + 4 (kf + 1) inverse and 12 + 2 kf forward fields per substage)."""
     import torch
     nx, ny, nz = w["nx"], w["ny"], w["nz"]
@@ -401,15 +417,40 @@ def cufft_comparison(L, w, stream, df_prof=None, steps=None, kf=4, reps=5):
             # cuFFT's most favourable form of the same synthesis / analysis
             out["cufft_%s_inverse" % name] = timed(lambda: torch.fft.irfft2(padded, s=(pz, px), norm="forward"), 1)
             out["cufft_%s_forward" % name] = timed(lambda: torch.fft.rfft2(real, norm="backward"), 1)
-            del padded, real
+            del padded
+            # pruned: batched 1D C2C transforms along z over the nx/2 retained kx columns only (the kz padding
+            # written into a zero buffer, inside the timed region), then batched C2R along x with the kx
+            # padding implicit (irfft's n = px); forward: R2C along x, the retained columns, C2C along z,
+            # the retained kz rows gathered. This is the strongest cuFFT form of the same work.
+            h = nz // 2
+            spec_c = torch.randn(ny, nz, nxh, dtype=cdt, device="cuda")
+            zbuf = torch.zeros(ny, pz, nx // 2, dtype=cdt, device="cuda")
+            spec_o = torch.zeros(ny, nz, nxh, dtype=cdt, device="cuda")
+
+            def pruned_inverse():
+                zbuf[:, :h] = spec_c[:, :h, :nx // 2]
+                zbuf[:, pz - h + 1:] = spec_c[:, h + 1:, :nx // 2]
+                t = torch.fft.ifft(zbuf, dim=1, norm="forward")
+                return torch.fft.irfft(t, n=px, dim=2, norm="forward")
+
+            def pruned_forward():
+                t = torch.fft.rfft(real, dim=2, norm="forward")[:, :, :nx // 2]
+                u = torch.fft.fft(t, dim=1, norm="forward")
+                spec_o[:, :h, :nx // 2] = u[:, :h]
+                spec_o[:, h + 1:, :nx // 2] = u[:, pz - h + 1:]
+
+            out["cufft_pruned_%s_inverse" % name] = timed(pruned_inverse, 1)
+            out["cufft_pruned_%s_forward" % name] = timed(pruned_forward, 1)
+            del real, spec_c, zbuf, spec_o
             torch.cuda.empty_cache()
     if df_prof and steps:
         n_inv, n_fwd = 8 + 4 * (kf + 1), 12 + 2 * kf
         out["lmvd_df_inverse"] = (df_prof["fft_z_inverse"][0] + df_prof["fft_x_inverse"][0]) / steps / n_inv
         out["lmvd_df_forward"] = (df_prof["fft_x_forward"][0] + df_prof["fft_z_forward"][0]) / steps / n_fwd
     return {"unit": "ms per field", "grid": [nx, ny, nz], "padded": [px, ny, pz], **out,
-            "note": "cuFFT transforms the whole padded field; this library skips the zero padding and the "
-                    "truncated modes and pairs two real rows per complex transform"}
+            "note": "cufft_*: whole padded field (irfft2 / rfft2); cufft_pruned_*: 1D C2C along z over the nx/2 "
+                    "retained columns and C2R / R2C along x, padding and truncation copies included; this library "
+                    "skips the zero padding and the truncated modes and pairs two real rows per complex transform"}
 
 
 def graphs_comparison(L, stream, grids=((32, 33, 32), (64, 65, 64), (128, 129, 128)), substages=40):
@@ -527,6 +568,7 @@ def run_cuda(args):
     stream = torch.cuda.Stream()
     st = {k: torch.from_numpy(np.ascontiguousarray(v)) for k, v in rt_state(**w).items()}
 
+    rates = measured_rates(L)
     res, final = time_variant(L, w, args.precision, args, stream, st, local, ws, e2e_steps=args.e2e_steps)
     ms_max, value = aggregate(res["ms"], npts * args.steps, ws, device="cuda")
     prof = res["prof"]
@@ -546,7 +588,8 @@ def run_cuda(args):
         "dtype": "f64", "data": "synthetic (seeded Rayleigh-Taylor-shaped state)", "config": config,
         "clocks": res["clocks"], "gpu_launches": int(res["launches"]),
         "device_bytes": res["device_bytes"],
-        "roofline": roofline_of(prof, res["ms"], args.precision, (w["nx"], w["ny"], w["nz"])), "e2e": e2e,
+        "roofline": roofline_of(prof, res["ms"], args.precision, (w["nx"], w["ny"], w["nz"]), rates), "e2e": e2e,
+        "issue_rates": {**rates, "unit": "operations/s", "source": "lmvd_rate_probe before the timed region"},
         "kernels": breakdown,
         "hbm_peak": {"gbs": hbm_peak_gbs()[0], "source": hbm_peak_gbs()[1],
                      "note": "kernels[*].hbm_frac = algorithmic bytes / time / this copy bandwidth"},
@@ -562,7 +605,7 @@ def run_cuda(args):
                           "FP64 solves / RHS / update"),
             "value": v2, "unit": UNIT, "ms_per_step": r2["ms"] / args.steps, "clocks": r2["clocks"],
             "device_bytes": r2["device_bytes"],
-            "roofline": roofline_of(r2["prof"], r2["ms"], other, (w["nx"], w["ny"], w["nz"])),
+            "roofline": roofline_of(r2["prof"], r2["ms"], other, (w["nx"], w["ny"], w["nz"]), rates),
             "kernels": {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps,
                             "tflops": (v[2] / (v[0] / 1e3) / 1e12) if v[0] > 0 else None}
                         for k, v in r2["prof"].items() if v[1] > 0},
@@ -584,8 +627,29 @@ def run_cuda(args):
         print(json.dumps(out))
 
 
+def print_rates(iters):
+    """The issue rates of this GPU (lmvd_rate_probe) with the SM clock sampled while they run."""
+    import torch
+
+    from paper_2206_09878_gb300 import lmvd as L
+    torch.cuda.set_device(0)
+    L.lmvd_rate_probe(0, 1000)   # module load and clock ramp
+    sampler = ClockSampler(0)
+    sampler.start()
+    rates = {n: L.lmvd_rate_probe(op, iters) for op, n in enumerate(("fp64_fma", "fp64_add", "fp64_mul", "fp32_fma"))}
+    clocks = sampler.stop()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    mhz = clocks.get("sm_mhz") or 2070.0
+    per = {n: v / (sms * mhz * 1e6) for n, v in rates.items()}
+    print(json.dumps({"unit": "operations/s", **rates, "per_clock_per_sm": per, "sms": sms, "iters": iters,
+                      "clocks": clocks, "fp64_peak_tflops_at_sampled_clock": 2 * rates["fp64_fma"] / 1e12}))
+
+
 def main():
     args = parse()
+    if args.rates:
+        print_rates(200000)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

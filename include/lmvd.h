@@ -50,6 +50,9 @@ extern "C" {
 #define LMVD_ERR_NONFINITE (-4)
 #define LMVD_ERR_UNSUPPORTED (-5)
 #define LMVD_ERR_FP_DIVERGED (-6)
+/* Only in the library built with index checks (liblmvd_check.so, -DLMVD_CHECK): a kernel found an index
+ * outside the array it was about to access and skipped that access. Latched by lmvd_synchronize. */
+#define LMVD_ERR_OUT_OF_BOUNDS (-7)
 
 /* Problem definition, copied at lmvd_create (all host values).
  * nx, nz      : Fourier grid (even; 3*nx/2 and 3*nz/2 must have no prime factors other than 2, 3).
@@ -192,18 +195,24 @@ int lmvd_forward_transform(lmvd_ctx* ctx, const double* phys, void* spec, int nf
 /* Allocation-free inverse transform (the paper has no counterpart: this serves callers that may not
  * allocate device memory at all -- code running under an allocator owned by another framework, or
  * after a start-up phase that forbids new allocations -- and therefore cannot create a context).
- * Computes exactly what lmvd_inverse_transform computes (FP64, same layouts) for an nx x ny x nz grid,
+ * Computes the same FP64 synthesis as lmvd_inverse_transform (same layouts) for an nx x ny x nz grid,
  * on cuda_stream (NULL = legacy default stream) of the current device, without any cudaMalloc: its
  * working memory is one static 32 MiB device array that every device loading the library holds until
- * the process exits. Limit: the twiddle tables plus ny * (3nz/2) * (nx/2) * 16 bytes must fit in the
- * 32 MiB (e.g. 128 x 129 x 128 fits; 256 x 257 x 256 does not).
+ * the process exits. Its twiddle factors are computed on the device (sincospi) where a context rounds
+ * long-double host values, so the two agree to rounding (relative max difference <= 1e-13 in the
+ * tests), not bit for bit. Limits: the twiddle tables plus ny * (3nz/2) * (nx/2) * 16 bytes must fit in
+ * the 32 MiB (e.g. 128 x 129 x 128 fits; 256 x 257 x 256 does not), and ny <= 65535 (one grid row of
+ * CTAs per y-plane).
  * spec, phys: caller-owned device memory. The first call on a device sets itself up (looks up the
  * array's device address, raises the kernels' shared-memory limit); make that first call before any
  * stream capture. All calls on a device share the array and leave their contents in it; calls whose
  * GPU work overlaps (different streams or host threads) race, so order them on one stream.
- * Errors: INVALID_ARG (NULL pointer, odd or too small nx/nz, nfields < 0, grid too large for the static
- * array), UNSUPPORTED (3nx/2 or 3nz/2 with prime factors other than 2 and 3, or above the limits of
- * lmvd_create), CUDA. */
+ * Launch errors: a launch error left pending on the calling host thread by earlier, unrelated work is
+ * cleared on entry (after the argument checks) and not reported; each of this call's launches is then
+ * checked, and the first failure returns CUDA without launching the rest.
+ * Errors: INVALID_ARG (NULL pointer, odd or too small nx/nz, ny < 1 or ny > 65535, nfields < 0, grid too
+ * large for the static array), UNSUPPORTED (3nx/2 or 3nz/2 with prime factors other than 2 and 3, or
+ * above the limits of lmvd_create), CUDA. */
 int lmvd_inverse_transform_noalloc(int nx, int ny, int nz, const void* spec, double* phys, int nfields,
                                    void* cuda_stream);
 
@@ -286,9 +295,15 @@ int lmvd_status(const lmvd_ctx* ctx);
 int lmvd_diagnostics_enable(lmvd_ctx* ctx, int on);
 
 /* Copies the record of the last substage (synchronous): out[0] = its substage index, out[1] = relative
- * mass residual, out[2 + k] = relative change of application k + 1 (k < k_f). Writes min(n, 2 + k_f)
- * values and returns 2 + k_f (the number available). The values are sums of atomics, not bitwise
- * reproducible. Errors: INVALID_ARG (NULL, n < 0, diagnostics never enabled), CUDA. */
+ * mass residual, out[2 + k] = relative change of application k + 1 (k < k_f), then
+ *   out[2 + k_f] = kinetic energy (1/2) integral of |m|^2 / rho dV of m = m^d + m^c at the substage's start
+ *     (the state's m^d and the substage's final m^c; x-z means on the padded grid, the y-integral of the
+ *     interpolant through the Greville values, times lx lz),
+ *   out[3 + k_f] = max over the padded grid of |m| (same m),
+ *   out[4 + k_f] = <m2^c> at y0 (the bottom value of the plane-mean curl-free momentum; Eq. mc_mean fixes
+ *     it to zero at y1, so this is the net mass flux the mean density change implies, Sec. 4.2).
+ * Writes min(n, 5 + k_f) values and returns 5 + k_f (the number available). The values are sums of
+ * atomics, not bitwise reproducible. Errors: INVALID_ARG (NULL, n < 0, diagnostics never enabled), CUDA. */
 int lmvd_diagnostics(lmvd_ctx* ctx, double* out, int n);
 
 /* Kernel accounting (no paper counterpart: observability of this implementation).
@@ -312,6 +327,20 @@ long long lmvd_kernel_launches(const lmvd_ctx* ctx);
 
 /* Static description of an error code. */
 const char* lmvd_strerror(int code);
+
+/* Issue rate of one arithmetic operation on the current device (no paper counterpart: it measures the
+ * denominators of the roofline fractions). op: 0 = FP64 FMA, 1 = FP64 add, 2 = FP64 multiply, 3 = FP32
+ * FMA. Runs 8 independent chains per thread, 8 CTAs of 256 threads per SM, iters iterations, after one
+ * shorter warm-up launch, on cuda_stream (NULL = legacy default stream), and writes the operations per
+ * second (CUDA-event time) to *ops_per_second. Synchronous; allocates and frees a small output array.
+ * Errors: INVALID_ARG (NULL output, iters < 1, op outside 0..3), OOM, CUDA. */
+int lmvd_rate_probe(int op, int iters, double* ops_per_second, void* cuda_stream);
+
+/* 1 if this library was built with the kernels' index checks (-DLMVD_CHECK, liblmvd_check.so), else 0
+ * (no paper counterpart: the checked build is a testing aid). In the checked build every checked access
+ * first tests its index against the extent of its array; a failed test skips the access and sets a
+ * device word that lmvd_synchronize turns into LMVD_ERR_OUT_OF_BOUNDS. The checks never trap. */
+int lmvd_checked_build(void);
 
 #ifdef __cplusplus
 }

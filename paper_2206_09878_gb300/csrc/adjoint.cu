@@ -24,6 +24,8 @@
 
 namespace lmvd {
 
+LMVD_DEFINE_OOB_TAKE(adj)
+
 struct AdjWork {
   void* arena = nullptr;
   size_t bytes = 0;
@@ -509,7 +511,7 @@ int adj_upload_band(AdjWork& A, const RowBand& m, DBand& d) {
   if (cudaMemcpy(c0, m.c0.data(), sizeof(int) * m.c0.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(v, m.v.data(), sizeof(double) * m.v.size(), cudaMemcpyHostToDevice) != cudaSuccess)
     return LMVD_ERR_CUDA;
-  d = DBand{c0, v, m.rows, m.w};
+  d = DBand{c0, v, m.rows, m.w, nullptr, m.cols};
   return LMVD_OK;
 }
 

@@ -20,6 +20,8 @@ struct lmvd_ctx {
 
 namespace lmvd {
 
+LMVD_DEFINE_OOB_TAKE(api)
+
 cudaEvent_t prof_begin(Ctx& c) {
   c.prof.launches++;
   if (!c.prof.on) return nullptr;
@@ -109,12 +111,22 @@ int upload(Ctx& c, const std::vector<T>& h, T** d) {
 int upload_band(Ctx& c, const RowBand& m, DBand& d) {
   int* c0;
   double* v;
+  df* vf;
   int e = upload(c, m.c0, &c0);
   if (e) return e;
   e = upload(c, m.v, &v);
   if (e) return e;
+  std::vector<df> split(m.v.size());
+  for (size_t q = 0; q < m.v.size(); ++q) {
+    const float hi = (float)m.v[q];
+    split[q] = df{hi, (float)(m.v[q] - (double)hi)};
+  }
+  e = upload(c, split, &vf);
+  if (e) return e;
   d.c0 = c0;
   d.v = v;
+  d.vf = vf;
+  d.cols = m.cols;
   d.rows = m.rows;
   d.w = m.w;
   return LMVD_OK;
@@ -309,9 +321,21 @@ void eval_jobs(Ctx& c, std::initializer_list<EvalJob> jobs) {
     fl += 4.0 * j.B.rows * j.B.w;
   }
   int maxrows = 0;
-  for (int q = 0; q < n; ++q) maxrows = std::max(maxrows, ej.j[q].B.rows);
-  LMVD_LAUNCH(c, KC_EVAL, fl * c.g.M, 16.0 * rows * c.g.M, k_eval,
-              dim3(mode_blocks(c.g), n, row_chunks(c.g, maxrows)), TPB_MODE, 0, c.g, ej);
+  bool acc = false;
+  for (int q = 0; q < n; ++q) {
+    maxrows = std::max(maxrows, ej.j[q].B.rows);
+    acc = acc || ej.j[q].acc;
+  }
+  int maxw = 0;
+  for (int q = 0; q < n; ++q) maxw = std::max(maxw, ej.j[q].B.w);
+  // the precision path evaluates the values that feed its transforms in double-float
+  if (c.cfg.precision == 1 && !acc && maxw >= 4 && maxw <= 9) {
+    const dim3 grid(mode_blocks(c.g), n, row_chunks(c.g, maxrows));
+    LMVD_LAUNCH_CALL(c, KC_EVAL, fl * c.g.M, 16.0 * rows * c.g.M,
+                     launch_eval_df(maxw, grid, TPB_MODE, c.stream, c.g, ej));
+  } else
+    LMVD_LAUNCH(c, KC_EVAL, fl * c.g.M, 16.0 * rows * c.g.M, k_eval,
+                dim3(mode_blocks(c.g), n, row_chunks(c.g, maxrows)), TPB_MODE, 0, c.g, ej);
 }
 
 // out = A^{-1} in (+ add) for each job; shared or per-mode factors; one or two threads per mode
@@ -347,9 +371,15 @@ void physical_pass_1(Ctx& c, double* const* zp = nullptr) {
   Fields8 o{};
   for (int f = 0; f < 8; ++f) o.p[f] = c.sv[f];
   const double SM = (double)c.g.ny * c.g.M;
-  LMVD_LAUNCH(c, KC_EVAL_P1, SM * (4.0 * 6 * c.B0g.w + 20.0), 16.0 * SM * 11 + 16.0 * c.g.M, k_eval_p1,
-              dim3(mode_blocks(c.g), row_chunks(c.g, c.g.ny)), TPB_MODE, 0, c.g, c.B0g, c.B1g, c.B2g, c.Sg0, c.Sg1,
-              c.z, c.om, c.m2, c.mm1, c.mm3, o);
+  if (c.cfg.precision == 1) {
+    const dim3 grid(mode_blocks(c.g), row_chunks(c.g, c.g.ny));
+    LMVD_LAUNCH_CALL(c, KC_EVAL_P1, SM * (4.0 * 6 * c.B0g.w + 20.0), 16.0 * SM * 11 + 16.0 * c.g.M,
+                     launch_eval_p1_df(c.cfg.spline_order, grid, TPB_MODE, c.stream, c.g, c.B0g, c.B1g, c.B2g, c.Sg0,
+                                       c.Sg1, c.z, c.om, c.m2, c.mm1, c.mm3, o));
+  } else
+    LMVD_LAUNCH(c, KC_EVAL_P1, SM * (4.0 * 6 * c.B0g.w + 20.0), 16.0 * SM * 11 + 16.0 * c.g.M, k_eval_p1,
+                dim3(mode_blocks(c.g), row_chunks(c.g, c.g.ny)), TPB_MODE, 0, c.g, c.B0g, c.B1g, c.B2g, c.Sg0,
+                c.Sg1, c.z, c.om, c.m2, c.mm1, c.mm3, o);
   // physical: z, zx, zz, zy, lapz -> pw[0..4]; m^d -> md[0..2]
   cd* in[8] = {c.sv[0], c.sv[1], c.sv[2], c.sv[3], c.sv[4], c.sv[5], c.sv[6], c.sv[7]};
   double* out[8] = {zf[0], zf[1], zf[2], zf[3], zf[4], c.md[0], c.md[1], c.md[2]};
@@ -476,7 +506,7 @@ void enqueue_substage(Ctx& c, const Tape* tape) {
   // step 3
   nvtxRangePop();
   nvtxRangePushA("step 3: fixed point, m^c");
-  if (c.diag_on) cudaMemsetAsync(c.ddiag, 0, sizeof(double) * (2 * KF_MAX_ADJ + 4), c.stream);
+  if (c.diag_on) cudaMemsetAsync(c.ddiag, 0, sizeof(double) * DIAG_N, c.stream);
   for (int k = 0; k < cf.kf; ++k) {
     // diagnostics: the change of this application (the previous iterate kept in sv[9], unused until pass 2)
     if (c.diag_on && k < KF_MAX_ADJ + 1)
@@ -504,6 +534,14 @@ void enqueue_substage(Ctx& c, const Tape* tape) {
   // C11-C13 and C22-C33 through pw[3..5], then u and rho into pw[0..3].
   struct Batch { int first, count, slot; };
   const Batch full[1] = {{0, 10, 0}}, lean[3] = {{0, 3, 3}, {3, 3, 3}, {6, 4, 0}};
+  if (c.diag_on) {
+    // kinetic energy and max |m| of m = m^d + m^c (before the products overwrite m^c), <m2^c> at y0
+    Fields3C mdf{{c.md[0], c.md[1], c.md[2]}}, mcf{{mcp[0], mcp[1], mcp[2]}};
+    LMVD_LAUNCH(c, KC_MISC, 10.0 * n, 8.0 * 7 * n, k_energy_norms, elem_blocks(n), 256, 0, g, c.wq, mdf, mcf,
+                c.invrho, cf.precision == 1 ? 1 : 0, c.ddiag + DIAG_KE,
+                reinterpret_cast<unsigned long long*>(c.ddiag + DIAG_MMAX));
+    cudaMemcpyAsync(c.ddiag + DIAG_MC2, c.m2c, sizeof(double), cudaMemcpyDeviceToDevice, c.stream);
+  }
   const Batch* batches = c.pw_n >= 10 ? full : lean;
   const int nb = c.pw_n >= 10 ? 1 : 3;
   for (int b = 0; b < nb; ++b) {
@@ -532,9 +570,15 @@ void enqueue_substage(Ctx& c, const Tape* tape) {
                c.lu_interp);
   Fields7C stc{};
   for (int f = 0; f < 7; ++f) stc.p[f] = c.st[f];
-  LMVD_LAUNCH(c, KC_RHS_EVAL, S * (4.0 * 6 * c.B1g.w + 4.0), 16.0 * 9 * S, k_rhs_eval,
-              dim3(mode_blocks(g), row_chunks(g, g.ny + 1)), TPB_MODE, 0,
-              g, c.B1g, c.B2g, c.Bs[0], c.Bs[1], c.Bs[2], c.Bs[3], stc, c.r_om, c.r_phi, c.r_m);
+  if (cf.precision == 1) {
+    const dim3 grid(mode_blocks(g), row_chunks(g, g.ny + 1));
+    LMVD_LAUNCH_CALL(c, KC_RHS_EVAL, S * (4.0 * 6 * c.B1g.w + 4.0), 16.0 * 9 * S,
+                     launch_rhs_eval_df(cf.spline_order, grid, TPB_MODE, c.stream, g, c.B1g, c.B2g, c.Bs, stc, c.r_om,
+                                        c.r_phi, c.r_m));
+  } else
+    LMVD_LAUNCH(c, KC_RHS_EVAL, S * (4.0 * 6 * c.B1g.w + 4.0), 16.0 * 9 * S, k_rhs_eval,
+                dim3(mode_blocks(g), row_chunks(g, g.ny + 1)), TPB_MODE, 0,
+                g, c.B1g, c.B2g, c.Bs[0], c.Bs[1], c.Bs[2], c.Bs[3], stc, c.r_om, c.r_phi, c.r_m);
   nvtxRangePop();
   nvtxRangePushA("step 6: RK2 update");
   // step 6: midpoint RK2, low-storage: (al, be) = (1/2, 0) at stage n, (1, -1/2) at stage '
@@ -788,6 +832,7 @@ int lmvd_create(const lmvd_config* cfg, void* stream, lmvd_ctx** out) {
     if (!err) err = upload_band(c, Ss0, c.Ss0);
     if (!err) err = upload_band(c, Ss2, c.Ss2);
     if (!err) err = upload(c, ds, &c.dstar);
+    if (!err) err = upload(c, greville_quadrature(kb, B0g), &c.wq);
     // shared LUs: interpolation / Dirichlet (values at g) and Neumann (dz/dy rows at the walls)
     const int Kb = std::max(half_width(B0g), half_width(B1g));
     if (Kb > KMAX) throw std::runtime_error("band");
@@ -1062,16 +1107,20 @@ int lmvd_synchronize(lmvd_ctx* h) {
     return latch(c, LMVD_ERR_CUDA);
   if (flags & 1u) latch(c, LMVD_ERR_NONFINITE);
   if (flags & 2u) latch(c, LMVD_ERR_FP_DIVERGED);
+  if (kCheckedBuild && (oob_take_api() | oob_take_fft() | oob_take_yk() | oob_take_pw() | oob_take_adj()))
+    latch(c, LMVD_ERR_OUT_OF_BOUNDS);
   return c.status;
 }
+
+int lmvd_checked_build(void) { return kCheckedBuild ? 1 : 0; }
 
 int lmvd_diagnostics_enable(lmvd_ctx* h, int on) {
   if (!h) return LMVD_ERR_INVALID_ARG;
   Ctx& c = h->c;
   if (on && !c.ddiag) {
-    const int e = device_alloc(c, (void**)&c.ddiag, sizeof(double) * (2 * KF_MAX_ADJ + 4));
+    const int e = device_alloc(c, (void**)&c.ddiag, sizeof(double) * DIAG_N);
     if (e) return latch(c, e);
-    cudaMemsetAsync(c.ddiag, 0, sizeof(double) * (2 * KF_MAX_ADJ + 4), c.stream);
+    cudaMemsetAsync(c.ddiag, 0, sizeof(double) * DIAG_N, c.stream);
   }
   c.diag_on = on != 0;
   return LMVD_OK;
@@ -1081,16 +1130,19 @@ int lmvd_diagnostics(lmvd_ctx* h, double* out, int n) {
   if (!h || !out || n < 0) return LMVD_ERR_INVALID_ARG;
   Ctx& c = h->c;
   if (!c.ddiag) return LMVD_ERR_INVALID_ARG;
-  double rec[2 * KF_MAX_ADJ + 4];
+  double rec[DIAG_N];
   if (cudaStreamSynchronize(c.stream) != cudaSuccess ||
       cudaMemcpy(rec, c.ddiag, sizeof(rec), cudaMemcpyDeviceToHost) != cudaSuccess)
     return latch(c, LMVD_ERR_CUDA);
   const int kf = std::min(c.cfg.kf, KF_MAX_ADJ + 1);
-  const int total = 2 + kf;
-  double vals[2 + KF_MAX_ADJ + 1];
+  const int total = 5 + kf;
+  double vals[5 + KF_MAX_ADJ + 1];
   vals[0] = c.s - 1;
   vals[1] = rec[1] > 0 ? std::sqrt(rec[0] / rec[1]) : 0.0;
   for (int k = 0; k < kf; ++k) vals[2 + k] = rec[3 + 2 * k] > 0 ? std::sqrt(rec[2 + 2 * k] / rec[3 + 2 * k]) : 0.0;
+  vals[2 + kf] = rec[DIAG_KE] * c.cfg.lx * c.cfg.lz;
+  vals[3 + kf] = std::sqrt(rec[DIAG_MMAX]);
+  vals[4 + kf] = rec[DIAG_MC2];
   for (int q = 0; q < std::min(n, total); ++q) out[q] = vals[q];
   return total;
 }
@@ -1137,6 +1189,7 @@ const char* lmvd_strerror(int code) {
     case LMVD_ERR_OOM: return "device out of memory";
     case LMVD_ERR_NONFINITE: return "non-finite value in the state";
     case LMVD_ERR_FP_DIVERGED: return "fixed-point iteration did not converge";
+    case LMVD_ERR_OUT_OF_BOUNDS: return "index out of bounds (checked build)";
     case LMVD_ERR_UNSUPPORTED: return "unsupported configuration";
     default: return "unknown error";
   }

@@ -41,6 +41,7 @@ __device__ inline size_t vidx(int i, size_t M, int m, int comp) {
 // L U x = in, then out = x (+ add). out may alias in; add may be null.
 template <class V>
 __device__ void band_solve_v(const DLU& f, int m, int mf, int comp, const V* in, const V* add, V* out, size_t M) {
+  if (!LMVD_IN(m, M) || (f.mstride && !LMVD_IN(mf, f.mstride)) || !LMVD_IN(f.K, KMAX + 1)) return;
   V win[KMAX];
 #pragma unroll
   for (int q = 0; q < KMAX; ++q) win[q] = vzero<V>();
@@ -80,6 +81,7 @@ __device__ void band_solve_v(const DLU& f, int m, int mf, int comp, const V* in,
 template <class V>
 __device__ void band_solve_T_v(const DLU& f, int m, int mf, int comp, const V* in, V* out, size_t M, int zlo,
                                int zhi) {
+  if (!LMVD_IN(m, M) || (f.mstride && !LMVD_IN(mf, f.mstride)) || !LMVD_IN(f.K, KMAX + 1)) return;
   V win[KMAX];
 #pragma unroll
   for (int q = 0; q < KMAX; ++q) win[q] = vzero<V>();
@@ -110,10 +112,12 @@ __device__ void band_solve_T_v(const DLU& f, int m, int mf, int comp, const V* i
 }
 
 __device__ inline double band_row_real(const DBand& B, int i, const double* x) {
+  double acc = 0.0;
+  if (!LMVD_IN(i, B.rows)) return acc;
   const int c = B.c0[i];
   const double* v = B.v + (size_t)i * B.w;
-  double acc = 0.0;
-  for (int q = 0; q < B.w; ++q) acc = fma(__ldg(v + q), x[c + q], acc);
+  for (int q = 0; q < B.w; ++q)
+    if (LMVD_IN(c + q, B.cols)) acc = fma(__ldg(v + q), x[c + q], acc);
   return acc;
 }
 

@@ -7,6 +7,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <stdexcept>
 
 namespace lmvd {
@@ -197,6 +198,22 @@ void band_profile(const DiagBand& A2, const DiagBand& A0, std::vector<int>& nl, 
     nu[i] = lst - i;
     if (nl[i] > K || nu[i] > K) throw std::runtime_error("fill-in beyond K");
   }
+}
+
+std::vector<double> greville_quadrature(const Knots& k, const RowBand& B0g) {
+  const int n = B0g.rows, p = k.order;
+  int K = 0;
+  for (int i = 0; i < n; ++i) K = std::max({K, std::abs(B0g.c0[i] - i), std::abs(B0g.c0[i] + B0g.w - 1 - i)});
+  const BandLU f = band_lu(transpose(to_diag(B0g, K)));
+  std::vector<double> w(n);
+  for (int j = 0; j < n; ++j) w[j] = (k.t[j + p] - k.t[j]) / p;
+  for (int i = 0; i < n; ++i)  // L y = b (unit lower)
+    for (int q = 1; q <= f.nl[i]; ++q) w[i] -= f.lo[(size_t)i * K + q - 1] * w[i - q];
+  for (int i = n - 1; i >= 0; --i) {  // U x = y
+    for (int r = 1; r <= f.nu[i]; ++r) w[i] -= f.up[(size_t)i * K + r - 1] * w[i + r];
+    w[i] *= f.invd[i];
+  }
+  return w;
 }
 
 BandLU band_lu(const DiagBand& A) {

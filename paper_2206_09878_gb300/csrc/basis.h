@@ -57,6 +57,10 @@ struct BandLU {
   std::vector<int> nl, nu;
 };
 BandLU band_lu(const DiagBand& A);
+// Weights w_i with sum_i w_i f(g_i) = integral over [y0, y1] of the order-p spline that interpolates f at
+// the Greville points g_i: w = A^{-T} b, A the collocation matrix (B0g), b_j = (t_{j+p} - t_j) / p the
+// integral of B_j.
+std::vector<double> greville_quadrature(const Knots& k, const RowBand& B0g);
 // Structural profile of L and U for the pattern union of A2 and A0 (no numerical values).
 void band_profile(const DiagBand& A2, const DiagBand& A0, std::vector<int>& nl, std::vector<int>& nu);
 

@@ -26,6 +26,8 @@
 
 namespace lmvd {
 
+LMVD_DEFINE_OOB_TAKE(fft)
+
 struct FieldsC {
   const cd* p[10];
 };
@@ -123,7 +125,7 @@ __device__ __forceinline__ void fft_stage(C* x, const FFTPlan& pl, int L, int tt
   for (int j = 0; j < NBT; ++j) {
     const int b = tt + j * tpt;
 #pragma unroll
-    for (int q = 0; q < R; ++q) v[j][q] = x[b + q * nb];
+    for (int q = 0; q < R; ++q) v[j][q] = LMVD_IN(b + q * nb, n) ? x[b + q * nb] : FT<C>::zero();
   }
   __syncthreads();
 #pragma unroll
@@ -131,6 +133,7 @@ __device__ __forceinline__ void fft_stage(C* x, const FFTPlan& pl, int L, int tt
     const int b = tt + j * tpt;
     const int k = pow2 ? (b & (L - 1)) : (b % L);
     const int base = (b - k) * R + k;
+    if (!LMVD_IN(base + (R - 1) * L, n)) continue;
     if (k) {
 #pragma unroll
       for (int q = 1; q < R; ++q) v[j][q] = F::template mulw<SIGN>(v[j][q], pl, q * k * tws);
@@ -204,7 +207,8 @@ __global__ void __launch_bounds__(FFT_CTA_Z, FFT_MIN_CTAS_Z) k_fft_z_inv(FFTPlan
     const int jz = idx / batch, bb = idx - jz * batch, kx = kx0 + bb;
     if (kx < h && jz != nz / 2) {
       const int pos = jz < nz / 2 ? jz : pz - nz + jz;
-      a[bb * ld + pos] = F::from_spec(src[(size_t)jz * g.nxh + kx]);
+      if (LMVD_IN(bb * ld + pos, batch * ld) && LMVD_IN((size_t)jz * g.nxh + kx, g.M))
+        a[bb * ld + pos] = F::from_spec(src[(size_t)jz * g.nxh + kx]);
     }
   }
   __syncthreads();
@@ -213,7 +217,8 @@ __global__ void __launch_bounds__(FFT_CTA_Z, FFT_MIN_CTAS_Z) k_fft_z_inv(FFTPlan
   C* dst = T + f * tstride + (size_t)j * pz * h;
   for (int idx = threadIdx.x; idx < pz * batch; idx += blockDim.x) {
     const int zz = idx / batch, bb = idx - zz * batch, kx = kx0 + bb;
-    if (kx < h) dst[(size_t)zz * h + kx] = res[bb * ld + zz];
+    if (kx < h && LMVD_IN((size_t)zz * h + kx, (size_t)pz * h) && LMVD_IN(bb * ld + zz, batch * ld))
+      dst[(size_t)zz * h + kx] = res[bb * ld + zz];
   }
 }
 
@@ -234,6 +239,7 @@ __global__ void __launch_bounds__(FFT_CTA_X, FFT_MIN_CTAS_X) k_fft_x_inv(FFTPlan
     const int bb = idx / h, k = idx - bb * h;
     const int za = 2 * (pr0 + bb), zb = za + 1;
     if (za >= pz) continue;
+    if (!LMVD_IN((size_t)za * h + k, (size_t)pz * h) || !LMVD_IN(bb * ld + px - 1, batch * ld)) continue;
     const C ta = src[(size_t)za * h + k];
     const C tb = zb < pz ? src[(size_t)zb * h + k] : F::zero();
     C* y = a + bb * ld;
@@ -252,6 +258,7 @@ __global__ void __launch_bounds__(FFT_CTA_X, FFT_MIN_CTAS_X) k_fft_x_inv(FFTPlan
     const int bb = idx / px, x = idx - bb * px;
     const int za = 2 * (pr0 + bb), zb = za + 1;
     if (za >= pz) continue;
+    if (!LMVD_IN((size_t)za * px + x, g.P) || !LMVD_IN(bb * ld + x, batch * ld)) continue;
     const C v = res[bb * ld + x];
     dst[(size_t)za * px + x] = F::re(v);
     if (zb < pz) dst[(size_t)zb * px + x] = F::im(v);
@@ -273,11 +280,11 @@ __global__ void __launch_bounds__(FFT_CTA_X, FFT_MIN_CTAS_X) k_fft_x_fwd(FFTPlan
     const int bb = idx / px, x = idx - bb * px;
     const int za = 2 * (pr0 + bb), zb = za + 1;
     R va = F::rzero(), vb = F::rzero();
-    if (za < pz) {
+    if (za < pz && LMVD_IN((size_t)za * px + x, g.P)) {
       va = src[(size_t)za * px + x];
       if (zb < pz) vb = src[(size_t)zb * px + x];
     }
-    a[bb * ld + x] = F::make(va, vb);
+    if (LMVD_IN(bb * ld + x, batch * ld)) a[bb * ld + x] = F::make(va, vb);
   }
   __syncthreads();
   fft_inplace<C, -1, EPT>(a + bt * ld, pl, tt, pl.tpt);
@@ -287,6 +294,7 @@ __global__ void __launch_bounds__(FFT_CTA_X, FFT_MIN_CTAS_X) k_fft_x_fwd(FFTPlan
     const int bb = idx / h, k = idx - bb * h;
     const int za = 2 * (pr0 + bb), zb = za + 1;
     if (za >= pz) continue;
+    if (!LMVD_IN((size_t)za * h + k, (size_t)pz * h) || !LMVD_IN(bb * ld + px - 1, batch * ld)) continue;
     const C yk = res[bb * ld + k];
     const C ym = F::cj(res[bb * ld + (k == 0 ? 0 : px - k)]);
     dst[(size_t)za * h + k] = F::half(F::add(yk, ym));
@@ -306,7 +314,8 @@ __global__ void __launch_bounds__(FFT_CTA_Z, FFT_MIN_CTAS_Z) k_fft_z_fwd(FFTPlan
   const C* src = T + f * tstride + (size_t)j * pz * h;
   for (int idx = threadIdx.x; idx < pz * batch; idx += blockDim.x) {
     const int zz = idx / batch, bb = idx - zz * batch, kx = kx0 + bb;
-    a[bb * ld + zz] = kx < h ? src[(size_t)zz * h + kx] : F::zero();
+    if (LMVD_IN(bb * ld + zz, batch * ld))
+      a[bb * ld + zz] = (kx < h && LMVD_IN((size_t)zz * h + kx, (size_t)pz * h)) ? src[(size_t)zz * h + kx] : F::zero();
   }
   __syncthreads();
   fft_inplace<C, -1, EPT>(a + bt * ld, pl, tt, pl.tpt);
@@ -316,8 +325,9 @@ __global__ void __launch_bounds__(FFT_CTA_Z, FFT_MIN_CTAS_Z) k_fft_z_fwd(FFTPlan
     const int jz = idx / batch, bb = idx - jz * batch, kx = kx0 + bb;
     if (kx > h) continue;
     cd v = mk(0, 0);
-    if (kx < h && jz != nz / 2) v = F::to_spec(res[bb * ld + (jz < nz / 2 ? jz : pz - nz + jz)], pl);
-    dst[(size_t)jz * g.nxh + kx] = v;
+    if (kx < h && jz != nz / 2 && LMVD_IN(bb * ld + (jz < nz / 2 ? jz : pz - nz + jz), batch * ld))
+      v = F::to_spec(res[bb * ld + (jz < nz / 2 ? jz : pz - nz + jz)], pl);
+    if (LMVD_IN((size_t)jz * g.nxh + kx, g.M)) dst[(size_t)jz * g.nxh + kx] = v;
   }
 }
 
@@ -545,6 +555,7 @@ extern "C" int lmvd_inverse_transform_noalloc(int nx, int ny, int nz, const void
   using namespace lmvd;
   if (!spec || !phys || nfields < 0 || ny < 1 || nx < 4 || nz < 4 || (nx % 2) || (nz % 2))
     return LMVD_ERR_INVALID_ARG;
+  if (ny > 65535) return LMVD_ERR_INVALID_ARG;  // ny is the grid's y-dimension (at most 65535 CTAs)
   Grid g{};
   g.nx = nx;
   g.ny = ny;
@@ -563,6 +574,8 @@ extern "C" int lmvd_inverse_transform_noalloc(int nx, int ny, int nz, const void
   const size_t off_tb = off_tz + align256(sizeof(double2) * g.pz);
   const size_t tbytes = sizeof(cd) * (size_t)ny * g.pz * (nx / 2);
   if (off_tb + tbytes > kNoAllocScratchBytes) return LMVD_ERR_INVALID_ARG;  // grid too large for the scratch
+  // a launch error left pending on this host thread by earlier work is not this call's to report
+  (void)cudaGetLastError();
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) return LMVD_ERR_CUDA;
   void* base = nullptr;
@@ -574,7 +587,9 @@ extern "C" int lmvd_inverse_transform_noalloc(int nx, int ny, int nz, const void
   fz.tw = (double2*)(sb + off_tz);
   cd* T = (cd*)(sb + off_tb);
   k_twiddles<<<(g.px + 255) / 256, 256, 0, st>>>(fx.tw, g.px);
+  if (cudaGetLastError() != cudaSuccess) return LMVD_ERR_CUDA;
   k_twiddles<<<(g.pz + 255) / 256, 256, 0, st>>>(fz.tw, g.pz);
+  if (cudaGetLastError() != cudaSuccess) return LMVD_ERR_CUDA;
   const size_t S = (size_t)ny * g.M, P = (size_t)ny * g.P;
   for (int f = 0; f < nfields; ++f) {
     FieldsC fi{};
@@ -584,9 +599,11 @@ extern "C" int lmvd_inverse_transform_noalloc(int nx, int ny, int nz, const void
     dim3 gz(cdiv(nx / 2, fz.batch), ny, 1);
     if (fz.ept == 12) k_fft_z_inv<cd, 12><<<gz, threads(fz), smem_bytes(fz), st>>>(fz, g, fi, T, 0);
     else k_fft_z_inv<cd, 6><<<gz, threads(fz), smem_bytes(fz), st>>>(fz, g, fi, T, 0);
+    if (cudaGetLastError() != cudaSuccess) return LMVD_ERR_CUDA;
     dim3 gx(cdiv(cdiv(g.pz, 2), fx.batch), ny, 1);
     if (fx.ept == 12) k_fft_x_inv<cd, 12><<<gx, threads(fx), smem_bytes(fx), st>>>(fx, g, T, 0, fo);
     else k_fft_x_inv<cd, 6><<<gx, threads(fx), smem_bytes(fx), st>>>(fx, g, T, 0, fo);
+    if (cudaGetLastError() != cudaSuccess) return LMVD_ERR_CUDA;
   }
-  return cudaGetLastError() == cudaSuccess ? LMVD_OK : LMVD_ERR_CUDA;
+  return LMVD_OK;
 }

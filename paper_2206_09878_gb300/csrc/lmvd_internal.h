@@ -13,6 +13,40 @@
 
 namespace lmvd {
 
+// ---------------------------------------------------------------- index checks (checked build)
+// Built with -DLMVD_CHECK (liblmvd_check.so), LMVD_IN(i, n) tests 0 <= i < n before an access: a failed
+// test sets bit 0 of this translation unit's device word and the access is skipped (no trap, the kernel
+// runs on). lmvd_synchronize reads and clears the words of every translation unit (oob_take_*) and latches
+// LMVD_ERR_OUT_OF_BOUNDS. In the normal build LMVD_IN is the constant true and costs nothing.
+#ifdef LMVD_CHECK
+static __device__ unsigned lmvd_oob_word;
+__device__ __forceinline__ bool lmvd_in(long long i, long long n) {
+  if (i >= 0 && i < n) return true;
+  atomicOr(&lmvd_oob_word, 1u);
+  return false;
+}
+#define LMVD_IN(i, n) ::lmvd::lmvd_in((long long)(i), (long long)(n))
+#define LMVD_DEFINE_OOB_TAKE(NAME)                                                                  \
+  unsigned oob_take_##NAME() {                                                                     \
+    unsigned v = 0, z = 0;                                                                          \
+    if (cudaMemcpyFromSymbol(&v, ::lmvd::lmvd_oob_word, sizeof v) != cudaSuccess) return 2u;        \
+    cudaMemcpyToSymbol(::lmvd::lmvd_oob_word, &z, sizeof z);                                        \
+    return v;                                                                                       \
+  }
+constexpr bool kCheckedBuild = true;
+#else
+#define LMVD_IN(i, n) true
+#define LMVD_DEFINE_OOB_TAKE(NAME) \
+  unsigned oob_take_##NAME() { return 0u; }
+constexpr bool kCheckedBuild = false;
+#endif
+// the index-check words of the translation units (0 in the normal build)
+unsigned oob_take_api();
+unsigned oob_take_fft();
+unsigned oob_take_yk();
+unsigned oob_take_pw();
+unsigned oob_take_adj();
+
 constexpr int KMAX = 8;   // widest band (each side) of any y-system LU supported
 // Device-memory budget of one context: the transform intermediate holds up to TBUF_FIELDS fields
 // (transforms of more fields run in chunks), there are up to PW_FIELDS physical work fields, and the RHS
@@ -38,11 +72,15 @@ __host__ __device__ inline cd times_i(cd a) { return cd{-a.im, a.re}; }         
 __host__ __device__ inline cd fma_rc(double s, cd x, cd acc) { return cd{fma(s, x.re, acc.re), fma(s, x.im, acc.im)}; }
 
 // ---------------------------------------------------------------- y-operators in device memory
-// Row-banded collocation matrix: row i covers columns c0[i] .. c0[i] + w - 1.
+// Row-banded collocation matrix: row i covers columns c0[i] .. c0[i] + w - 1. vf holds the same entries
+// as double-float pairs (hi = v rounded to a float, lo = the remainder rounded to a float) for the
+// evaluations of the precision path.
 struct DBand {
   const int* c0;
   const double* v;
   int rows, w;
+  const df* vf;
+  int cols;  // rows of the array a row of the band reads (index checks of the checked build)
 };
 // LU factors of band systems, K entries per row (zeros outside the profile nl / nu). Shared factors:
 // mstride = 0, element (i, q) at [i * K + q]; per-mode factors: element (i, q) of factor mode mf at
@@ -117,10 +155,12 @@ inline unsigned row_chunks(const Grid& g, int rows) {
 inline int solve_split(const Grid& g) { return g.M < 65536 ? 2 : 1; }
 
 __device__ inline cd band_row(const DBand& B, int i, const cd* x, size_t M, int m) {
+  cd acc = mk(0, 0);
+  if (!LMVD_IN(i, B.rows) || !LMVD_IN(m, M)) return acc;
   const int c = B.c0[i];
   const double* v = B.v + (size_t)i * B.w;
-  cd acc = mk(0, 0);
-  for (int q = 0; q < B.w; ++q) acc = fma_rc(__ldg(v + q), x[(size_t)(c + q) * M + m], acc);
+  for (int q = 0; q < B.w; ++q)
+    if (LMVD_IN(c + q, B.cols)) acc = fma_rc(__ldg(v + q), x[(size_t)(c + q) * M + m], acc);
   return acc;
 }
 
@@ -171,6 +211,8 @@ struct Prof {
 
 // ---------------------------------------------------------------- adjoint support
 constexpr int KF_MAX_ADJ = 15;
+constexpr int DIAG_KE = 2 * KF_MAX_ADJ + 4, DIAG_MMAX = DIAG_KE + 1, DIAG_MC2 = DIAG_KE + 2;
+constexpr int DIAG_N = DIAG_KE + 4;  // doubles in the diagnostics record
 // Physical fields of one forward substage that the adjoint of the products needs.
 struct Tape {
   double* zp[5];                   // z, dz/dx, dz/dz, dz/dy, lap z (pass 1)
@@ -224,9 +266,12 @@ struct Ctx {
   unsigned* dflags = nullptr;  // device status word: bit 0 = a non-finite value in the state (k_check_finite),
                                // bit 1 = the fixed point did not converge (diagnostics on)
   // diagnostics record of the last substage (lmvd_diagnostics): [0, 1] = |mass residual|^2, |rho_t|^2,
-  // [2 + 2k, 3 + 2k] = |dz/dt^{k+1} - dz/dt^k|^2, |dz/dt^{k+1}|^2 for k < kf
+  // [2 + 2k, 3 + 2k] = |dz/dt^{k+1} - dz/dt^k|^2, |dz/dt^{k+1}|^2 for k < kf; [DIAG_KE] = kinetic energy,
+  // [DIAG_MMAX] = max |m|^2 over the grid (the bits of a non-negative double, ordered as an integer),
+  // [DIAG_MC2] = <m2^c> at y0
   bool diag_on = false;
   double* ddiag = nullptr;
+  double* wq = nullptr;  // ny quadrature weights at the Greville points (integral of the interpolant)
 
   // CUDA graphs of one substage (lmvd_graphs_enable), one per launch pattern (see graph_key in api.cu)
   static constexpr int GRAPH_KEY = 23;
@@ -264,6 +309,14 @@ void prof_end(Ctx& c, int cls, cudaEvent_t a, double flops, double bytes);
     cudaEvent_t ev_a_ = ::lmvd::prof_begin(C);                              \
     KERN<<<GRID, BLOCK, SMEM, (C).stream>>>(__VA_ARGS__);                   \
     ::lmvd::prof_end(C, CLS, ev_a_, (double)(FLOPS), (double)(BYTES));      \
+  } while (0)
+
+// The same accounting around a call that launches exactly one kernel on (C).stream.
+#define LMVD_LAUNCH_CALL(C, CLS, FLOPS, BYTES, CALL)                     \
+  do {                                                                  \
+    cudaEvent_t ev_a_ = ::lmvd::prof_begin(C);                          \
+    CALL;                                                               \
+    ::lmvd::prof_end(C, CLS, ev_a_, (double)(FLOPS), (double)(BYTES));  \
   } while (0)
 
 // ---------------------------------------------------------------- launchers (defined in .cu files)

@@ -9,6 +9,8 @@
 
 namespace lmvd {
 
+LMVD_DEFINE_OOB_TAKE(pw)
+
 // rho, 1/rho, f'(z) = rho^2 (rh - rl) / (rl rh), w = grad z / rho, and
 // R_z = (-m^d . grad z + (rho D_z) lap z) / rho with rho D_z = kappa constant (Sc = 1 setting).
 __global__ void k_products_p1(size_t n, EosArgs e, const double* zp, const double* zx, const double* zz,

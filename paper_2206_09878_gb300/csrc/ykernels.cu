@@ -9,6 +9,8 @@
 
 namespace lmvd {
 
+LMVD_DEFINE_OOB_TAKE(yk)
+
 // ------------------------------------------------------------------ step 1-2 inputs: values at g
 // out[0..7] = z, dz/dx, dz/dz, dz/dy, lap z, m1^d, m2^d, m3^d at the Greville points of the order-p space.
 // m1^d, m3^d follow Eq. md_recon with d m2^d / dy evaluated directly from the order-(p+1) space;
@@ -73,6 +75,269 @@ __global__ void k_eval(Grid g, EvalJobs jobs) {
   }
   for (int i = r0; i < r1; ++i)
     jb.out[(size_t)i * M + m] = ny ? mk(0, 0) : band_row(jb.B, i, jb.in, M, m);
+}
+
+// ------------------------------------------------------------------ evaluations in double-float
+// The precision path (precision = 1) evaluates the B-spline sums that feed the inverse transforms and the
+// right-hand sides that follow the forward transforms in double-float on the FP32 pipe: the band entries
+// come as pairs (DBand.vf), each complex double input is split with integer operations, the products are
+// accumulated without renormalisation (error <= ~w 2^-48 of the sum of |terms|), and the result is
+// renormalised and rounded back to a double with integer operations. The per-mode multipliers (i k1,
+// 1/k^2, ...) are applied in double-float too, so these kernels issue no FP64 instruction per term.
+
+// acc + b * x without renormalisation: TwoProd by FMA, TwoSum of the high parts, low parts summed
+__device__ __forceinline__ df dfma_lazy(df b, df x, df acc) {
+  const float p = __fmul_rn(b.hi, x.hi);
+  float e = __fmaf_rn(b.hi, x.hi, -p);
+  e = __fmaf_rn(b.hi, x.lo, e);
+  e = __fmaf_rn(b.lo, x.hi, e);
+  float s, t;
+  two_sum(acc.hi, p, s, t);
+  return df{s, __fadd_rn(__fadd_rn(acc.lo, e), t)};
+}
+__device__ __forceinline__ df drenorm(df a) {
+  float s, e;
+  two_sum(a.hi, a.lo, s, e);
+  return df{s, e};
+}
+__device__ __forceinline__ cdf cd_to_cdf(cd x) { return cdf{df_from_double_int(x.re), df_from_double_int(x.im)}; }
+__device__ __forceinline__ cd cdf_to_cd(cdf x) {
+  return cd{df_to_double_int(drenorm(x.re)), df_to_double_int(drenorm(x.im))};
+}
+// A thread walks the rows of one mode, and a band's first column c0[i] never decreases and grows by at
+// most one per row (Greville points are at most one knot interval apart), so each input coefficient is
+// split into a double-float pair once and kept in a register window of the W columns c .. c + W - 1
+// (W = the band width) instead of once per band entry that reads it.
+template <int W>
+struct DfWin {
+  cdf v[W];
+  int c = -(1 << 30);
+  cd pre;             // the raw coefficient of column pre_col, loaded one row ahead
+  int pre_col = -1;
+  __device__ __forceinline__ cdf fetch(const cd* x, size_t M, int m, int col, int cols) const {
+    if (col == pre_col) return cd_to_cdf(pre);
+    return (col < cols && LMVD_IN(col, cols)) ? cd_to_cdf(x[(size_t)col * M + m]) : cdf{};
+  }
+  __device__ __forceinline__ void load(const cd* x, size_t M, int m, int c0, int cols) {
+    c = c0;
+#pragma unroll
+    for (int q = 0; q < W; ++q) v[q] = fetch(x, M, m, c0 + q, cols);
+  }
+  // move the window to start at column c0
+  __device__ __forceinline__ void seek(const cd* x, size_t M, int m, int c0, int cols) {
+    if (c0 < c || c0 > c + 2) {
+      load(x, M, m, c0, cols);
+      return;
+    }
+    while (c < c0) {
+#pragma unroll
+      for (int q = 0; q < W - 1; ++q) v[q] = v[q + 1];
+      v[W - 1] = fetch(x, M, m, c + W, cols);
+      ++c;
+    }
+  }
+  // issue the load of the column the next row's window adds (its first column is c_next), so that its
+  // latency overlaps this row's arithmetic; a thread otherwise has a single load in flight
+  __device__ __forceinline__ void prefetch(const cd* x, size_t M, int m, int c_next, int cols) {
+    const int col = c_next + W - 1;
+    if (c_next > c && col > c + W - 1 && col != pre_col && col < cols && LMVD_IN(col, cols)) {
+      pre = x[(size_t)col * M + m];
+      pre_col = col;
+    }
+  }
+  // sum over q < w of b[q] v[q] (lazy accumulation)
+  __device__ __forceinline__ cdf dot(const DBand& B, int i) const {
+    const float2* b = reinterpret_cast<const float2*>(B.vf) + (size_t)i * B.w;
+    df ar{0.f, 0.f}, ai{0.f, 0.f};
+#pragma unroll
+    for (int q = 0; q < W; ++q)
+      if (q < B.w) {
+        const float2 bq = __ldg(b + q);
+        const df bb{bq.x, bq.y};
+        ar = dfma_lazy(bb, v[q].re, ar);
+        ai = dfma_lazy(bb, v[q].im, ai);
+      }
+    return cdf{ar, ai};
+  }
+};
+__device__ __forceinline__ cdf cdf_add_lazy(cdf a, cdf b) { return cdf{dadd_lazy(a.re, b.re), dadd_lazy(a.im, b.im)}; }
+__device__ __forceinline__ df df_of(double x) { return df_from_double_int(x); }
+
+// k_eval_p1 in double-float (same outputs, same layout, FP64 values); WB: width of the order-p bands (B0g,
+// B1g, B2g, one window each for z and Omega2), WS: of the order-(p+1) ones (Sg0, Sg1; one window for m2)
+template <int WB, int WS>
+__global__ void __launch_bounds__(128) k_eval_p1_df(Grid g, DBand B0g, DBand B1g, DBand B2g, DBand Sg0, DBand Sg1,
+                                                    const cd* z, const cd* om, const cd* m2, const double* mm1,
+                                                    const double* mm3, Fields8 out) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= (int)g.M) return;
+  const size_t M = g.M;
+  int r0, r1;
+  row_range(g.ny, blockIdx.y, gridDim.y, r0, r1);
+  if (is_nyquist(g, m)) {
+    for (int i = r0; i < r1; ++i)
+      for (int f = 0; f < 8; ++f) out.p[f][(size_t)i * M + m] = mk(0, 0);
+    return;
+  }
+  if (m == 0) {  // the plane means and the k = 0 z values: one mode, kept in FP64
+    for (int i = r0; i < r1; ++i) {
+      const size_t o = (size_t)i * M;
+      out.p[0][o] = band_row(B0g, i, z, M, 0);
+      out.p[1][o] = mk(0, 0);
+      out.p[2][o] = mk(0, 0);
+      out.p[3][o] = band_row(B1g, i, z, M, 0);
+      out.p[4][o] = band_row(B2g, i, z, M, 0);
+      out.p[5][o] = mk(band_row_real(B0g, i, mm1), 0.0);
+      out.p[6][o] = mk(0, 0);
+      out.p[7][o] = mk(band_row_real(B0g, i, mm3), 0.0);
+    }
+    return;
+  }
+  double k1d, k3d;
+  wavenumbers(g, m, k1d, k3d);
+  const double k2d = k1d * k1d + k3d * k3d;
+  // per-mode multipliers, split once (one FP64 division per mode, none per row)
+  const df k1 = df_of(k1d), k3 = df_of(k3d), nk2 = df_of(-k2d), ik2 = df_of(1.0 / k2d);
+  const df nk1 = dneg(k1), nk3 = dneg(k3);
+  DfWin<WB> wz, wo;
+  DfWin<WS> wm;
+  for (int i = r0; i < r1; ++i) {
+    if (!LMVD_IN(i, B0g.rows) || !LMVD_IN(i, Sg0.rows)) continue;
+    const size_t o = (size_t)i * M + m;
+    const int cb = __ldg(B0g.c0 + i), cs = __ldg(Sg0.c0 + i);
+    wz.seek(z, M, m, cb, B0g.cols);
+    wo.seek(om, M, m, cb, B0g.cols);
+    wm.seek(m2, M, m, cs, Sg0.cols);
+    if (i + 1 < r1) {
+      const int nb = __ldg(B0g.c0 + i + 1), ns = __ldg(Sg0.c0 + i + 1);
+      wz.prefetch(z, M, m, nb, B0g.cols);
+      wo.prefetch(om, M, m, nb, B0g.cols);
+      wm.prefetch(m2, M, m, ns, Sg0.cols);
+    }
+    const cdf zg = wz.dot(B0g, i), zy = wz.dot(B1g, i), zyy = wz.dot(B2g, i);
+    const cdf dm2 = wm.dot(Sg1, i), omg = wo.dot(B0g, i);
+    const cdf zgr{drenorm(zg.re), drenorm(zg.im)};
+    out.p[0][o] = cdf_to_cd(zgr);
+    out.p[1][o] = cdf_to_cd(cdf{dmul(nk1, zgr.im), dmul(k1, zgr.re)});   // i k1 z
+    out.p[2][o] = cdf_to_cd(cdf{dmul(nk3, zgr.im), dmul(k3, zgr.re)});   // i k3 z
+    out.p[3][o] = cdf_to_cd(zy);
+    out.p[4][o] = cdf_to_cd(cdf_add_lazy(cdf{dmul(nk2, zgr.re), dmul(nk2, zgr.im)}, zyy));  // -k^2 z + z''
+    const cdf dmr{drenorm(dm2.re), drenorm(dm2.im)}, omr{drenorm(omg.re), drenorm(omg.im)};
+    // m1^d = (i k1 dm2 - i k3 om) / k^2, m3^d = (i k3 dm2 + i k1 om) / k^2 (Eq. md_recon)
+    const df a1 = ddot2(k1, dmr.re, nk3, omr.re), b1 = ddot2(k1, dmr.im, nk3, omr.im);
+    const df a3 = ddot2(k3, dmr.re, k1, omr.re), b3 = ddot2(k3, dmr.im, k1, omr.im);
+    out.p[5][o] = cdf_to_cd(cdf{dmul(ik2, dneg(b1)), dmul(ik2, a1)});
+    out.p[6][o] = cdf_to_cd(wm.dot(Sg0, i));
+    out.p[7][o] = cdf_to_cd(cdf{dmul(ik2, dneg(b3)), dmul(ik2, a3)});
+  }
+}
+
+// k_eval in double-float (jobs without accumulation into out); W: the widest band of the jobs
+template <int W>
+__global__ void __launch_bounds__(128) k_eval_df(Grid g, EvalJobs jobs) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= (int)g.M) return;
+  const EvalJob& jb = jobs.j[blockIdx.y];
+  const size_t M = g.M;
+  const bool ny = is_nyquist(g, m);
+  int r0, r1;
+  row_range(jb.B.rows, blockIdx.z, gridDim.z, r0, r1);
+  DfWin<W> win;
+  for (int i = r0; i < r1; ++i) {
+    if (ny) {
+      jb.out[(size_t)i * M + m] = mk(0, 0);
+      continue;
+    }
+    win.seek(jb.in, M, m, __ldg(jb.B.c0 + i), jb.B.cols);
+    if (i + 1 < r1) win.prefetch(jb.in, M, m, __ldg(jb.B.c0 + i + 1), jb.B.cols);
+    jb.out[(size_t)i * M + m] = cdf_to_cd(win.dot(jb.B, i));
+  }
+}
+
+// k_rhs_eval in double-float; the k = 0 mean right-hand sides stay in FP64 (one mode). WB: band width of the
+// order-p space (B1g, B2g at g; Bs0..Bs3 at g*). Two sweeps: R_Omega2 (two windows), then R_phi2 (four).
+template <int WB>
+__global__ void __launch_bounds__(128) k_rhs_eval_df(Grid g, DBand B1g, DBand B2g, DBand Bs0, DBand Bs1, DBand Bs2,
+                                                     DBand Bs3, Fields7C st, cd* r_om, cd* r_phi, double* r_m) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= (int)g.M) return;
+  const size_t M = g.M;
+  const int ny = g.ny;
+  int r0, r1;
+  row_range(ny + 1, blockIdx.y, gridDim.y, r0, r1);
+  if (m == 0 || is_nyquist(g, m)) {
+    for (int i = r0; i < r1; ++i) {
+      if (i < ny) r_om[(size_t)i * M + m] = mk(0, 0);
+      r_phi[(size_t)i * M + m] = mk(0, 0);
+      if (m == 0 && i < ny) {
+        r_m[i] = (band_row(B1g, i, st.p[1], M, 0) + band_row(B2g, i, st.p[2], M, 0)).re;
+        r_m[ny + i] = (band_row(B1g, i, st.p[4], M, 0) + band_row(B2g, i, st.p[5], M, 0)).re;
+      }
+    }
+    return;
+  }
+  {
+    DfWin<WB> w1, w2;
+    for (int i = r0; i < min(r1, ny); ++i) {
+      const int c = __ldg(B1g.c0 + i);
+      w1.seek(st.p[1], M, m, c, B1g.cols);
+      w2.seek(st.p[2], M, m, c, B2g.cols);
+      if (i + 1 < min(r1, ny)) {
+        const int cn = __ldg(B1g.c0 + i + 1);
+        w1.prefetch(st.p[1], M, m, cn, B1g.cols);
+        w2.prefetch(st.p[2], M, m, cn, B2g.cols);
+      }
+      const cdf a = cdf_add_lazy(w1.dot(B1g, i), w2.dot(B2g, i));
+      r_om[(size_t)i * M + m] = cdf_to_cd(cdf_add_lazy(a, cd_to_cdf(st.p[0][(size_t)i * M + m])));
+    }
+  }
+  DfWin<WB> w3, w4, w5, w6;
+  for (int i = r0; i < r1; ++i) {
+    const int c = __ldg(Bs0.c0 + i);
+    w3.seek(st.p[3], M, m, c, Bs0.cols);
+    w4.seek(st.p[4], M, m, c, Bs1.cols);
+    w5.seek(st.p[5], M, m, c, Bs2.cols);
+    w6.seek(st.p[6], M, m, c, Bs3.cols);
+    if (i + 1 < r1) {
+      const int cn = __ldg(Bs0.c0 + i + 1);
+      w3.prefetch(st.p[3], M, m, cn, Bs0.cols);
+      w4.prefetch(st.p[4], M, m, cn, Bs1.cols);
+      w5.prefetch(st.p[5], M, m, cn, Bs2.cols);
+      w6.prefetch(st.p[6], M, m, cn, Bs3.cols);
+    }
+    const cdf b = cdf_add_lazy(w3.dot(Bs0, i), w4.dot(Bs1, i));
+    const cdf d = cdf_add_lazy(w5.dot(Bs2, i), w6.dot(Bs3, i));
+    r_phi[(size_t)i * M + m] = cdf_to_cd(cdf_add_lazy(b, d));
+  }
+}
+
+// launchers for spline orders 4..8 (band widths 4..9); api.cu brackets them with its launch accounting
+void launch_eval_p1_df(int p, dim3 grid, int tpb, cudaStream_t st, const Grid& g, const DBand& B0g, const DBand& B1g,
+                       const DBand& B2g, const DBand& Sg0, const DBand& Sg1, const cd* z, const cd* om, const cd* m2,
+                       const double* mm1, const double* mm3, const Fields8& out) {
+  switch (p) {
+#define LMVD_P1(P) \
+    case P: k_eval_p1_df<P, P + 1><<<grid, tpb, 0, st>>>(g, B0g, B1g, B2g, Sg0, Sg1, z, om, m2, mm1, mm3, out); break;
+    LMVD_P1(4) LMVD_P1(5) LMVD_P1(6) LMVD_P1(7) LMVD_P1(8)
+#undef LMVD_P1
+  }
+}
+void launch_eval_df(int w, dim3 grid, int tpb, cudaStream_t st, const Grid& g, const EvalJobs& jobs) {
+  switch (w) {
+#define LMVD_EV(W) \
+    case W: k_eval_df<W><<<grid, tpb, 0, st>>>(g, jobs); break;
+    LMVD_EV(4) LMVD_EV(5) LMVD_EV(6) LMVD_EV(7) LMVD_EV(8) LMVD_EV(9)
+#undef LMVD_EV
+  }
+}
+void launch_rhs_eval_df(int p, dim3 grid, int tpb, cudaStream_t st, const Grid& g, const DBand& B1g, const DBand& B2g,
+                        const DBand* Bs, const Fields7C& stc, cd* r_om, cd* r_phi, double* r_m) {
+  switch (p) {
+#define LMVD_RE(P) \
+    case P: k_rhs_eval_df<P><<<grid, tpb, 0, st>>>(g, B1g, B2g, Bs[0], Bs[1], Bs[2], Bs[3], stc, r_om, r_phi, r_m); break;
+    LMVD_RE(4) LMVD_RE(5) LMVD_RE(6) LMVD_RE(7) LMVD_RE(8)
+#undef LMVD_RE
+  }
 }
 
 // ------------------------------------------------------------------ banded solves
@@ -153,6 +418,7 @@ __global__ void k_mc_post(Grid g, const double* dstar, const cd* rt, cd* m1c, cd
   wavenumbers(g, m, k1, k3);
   const double k = sqrt(k1 * k1 + k3 * k3), ik = 1.0 / k;
   for (int i = r0; i < r1; ++i) {
+    if (!LMVD_IN(i + 1, ny + 1)) continue;
     const cd x = m2c[(size_t)i * M + m], xn = m2c[(size_t)(i + 1) * M + m];
     const cd dm = __ldg(dstar + i) * (xn - x);
     const cd mpar = ik * times_i(rt[(size_t)i * M + m] + dm);
@@ -389,6 +655,33 @@ __global__ void k_mass_norms(Grid g, const double* dstar, const cd* rt, const cd
   }
   block_add(d, out);
   block_add(s, out + 1);
+}
+
+// Kinetic energy (1/2) integral of |m|^2 / rho over the domain and max |m|^2 over the grid, m = m^d + m^c on the
+// padded grid. A plane's mean of a product on the 3/2 grid is the k = 0 coefficient of the dealiased product;
+// the y-integral uses the quadrature weights of the Greville interpolant (wq), and the x-z area lx lz is
+// applied on the host. df_fields: the physical fields hold double-float pairs (precision 1).
+__device__ __forceinline__ double phys_value(const double* p, size_t o, int df_fields) {
+  if (!df_fields) return p[o];
+  const float2 v = reinterpret_cast<const float2*>(p)[o];
+  return (double)v.x + (double)v.y;
+}
+__global__ void k_energy_norms(Grid g, const double* wq, Fields3C md, Fields3C mc, const double* invrho, int df_fields,
+                               double* ke, unsigned long long* m2max) {
+  const size_t n = (size_t)g.ny * g.P;
+  double e = 0.0, mx = 0.0;
+  for (size_t o = blockIdx.x * (size_t)blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x) {
+    double mm = 0.0;
+    for (int c = 0; c < 3; ++c) {
+      const double m = phys_value(md.p[c], o, df_fields) + phys_value(mc.p[c], o, df_fields);
+      mm = fma(m, m, mm);
+    }
+    e = fma(0.5 * __ldg(wq + o / g.P) * mm, phys_value(invrho, o, df_fields), e);
+    mx = fmax(mx, mm);
+  }
+  block_add(e / (double)g.P, ke);
+  for (int q = 16; q > 0; q >>= 1) mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, q));
+  if ((threadIdx.x & 31) == 0) atomicMax(m2max, (unsigned long long)__double_as_longlong(mx));
 }
 
 // bit 1 of *flag if the last (the kf-th) fixed-point application, recorded at diag[2 kf], diag[2 kf + 1],

@@ -53,10 +53,23 @@ __global__ void k_diff_norms(size_t n, const cd* a, const cd* b, double* out);
 __global__ void k_mass_norms(Grid g, const double* dstar, const cd* rt, const cd* m1, const cd* m2, const cd* m3,
                              double* out);
 __global__ void k_fp_check(const double* diag, int kf, unsigned* flag);
+struct Fields3C {
+  const double* p[3];
+};
+__global__ void k_energy_norms(Grid g, const double* wq, Fields3C md, Fields3C mc, const double* invrho, int df_fields,
+                               double* ke, unsigned long long* m2max);
 
 __global__ void k_eval_p1(Grid g, DBand B0g, DBand B1g, DBand B2g, DBand Sg0, DBand Sg1, const cd* z,
                           const cd* om, const cd* m2, const double* mm1, const double* mm3, Fields8 out);
 __global__ void k_eval(Grid g, EvalJobs jobs);
+// double-float evaluations of the precision path (same outputs as k_eval_p1, k_eval without accumulation and
+// k_rhs_eval), launched on st for spline orders p = 4..8 (band widths w = 4..9)
+void launch_eval_p1_df(int p, dim3 grid, int tpb, cudaStream_t st, const Grid& g, const DBand& B0g, const DBand& B1g,
+                       const DBand& B2g, const DBand& Sg0, const DBand& Sg1, const cd* z, const cd* om, const cd* m2,
+                       const double* mm1, const double* mm3, const Fields8& out);
+void launch_eval_df(int w, dim3 grid, int tpb, cudaStream_t st, const Grid& g, const EvalJobs& jobs);
+void launch_rhs_eval_df(int p, dim3 grid, int tpb, cudaStream_t st, const Grid& g, const DBand& B1g, const DBand& B2g,
+                        const DBand* Bs, const Fields7C& stc, cd* r_om, cd* r_phi, double* r_m);
 __global__ void k_solve_cd(Grid g, DLU lu, SolveJobs jobs);
 __global__ void k_solve_re(Grid g, DLU lu, SolveJobs jobs);
 __global__ void k_mc_rhs(Grid g, DBand Bs1, const cd* rt, cd* m2c);

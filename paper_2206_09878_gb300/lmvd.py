@@ -11,7 +11,8 @@ import os
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "liblmvd.so")
+# LMVD_LIBRARY selects another build of the same library, e.g. the index-checked liblmvd_check.so
+LIB_PATH = os.environ.get("LMVD_LIBRARY") or os.path.join(_HERE, "liblmvd.so")
 
 LMVD_FIELD_RZ = 0
 LMVD_FIELD_ZDOT = 1
@@ -76,6 +77,8 @@ def _load():
         "lmvd_graphs_enable": (I, [P, I]),
         "lmvd_graph_count": (I, [P]),
         "lmvd_df64_convert": (I, [P, P, P, P, P, P, S, P]),
+        "lmvd_checked_build": (I, []),
+        "lmvd_rate_probe": (I, [I, I, ctypes.POINTER(ctypes.c_double), P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -93,7 +96,8 @@ EXPORTED = ("lmvd_default_config", "lmvd_create", "lmvd_destroy", "lmvd_set_stat
             "lmvd_profile_read", "lmvd_kernel_class_name", "lmvd_kernel_launches", "lmvd_inverse_transform",
             "lmvd_forward_transform", "lmvd_inverse_transform_noalloc", "lmvd_state_bytes",
             "lmvd_adjoint_substage", "lmvd_adjoint_startup", "lmvd_device_bytes", "lmvd_diagnostics_enable",
-            "lmvd_diagnostics", "lmvd_graphs_enable", "lmvd_graph_count", "lmvd_df64_convert")
+            "lmvd_diagnostics", "lmvd_graphs_enable", "lmvd_graph_count", "lmvd_df64_convert",
+            "lmvd_checked_build", "lmvd_rate_probe")
 LMVD_KERNEL_CLASSES = 13
 
 
@@ -216,6 +220,19 @@ def lmvd_inverse_transform_noalloc(nx, ny, nz, spec, phys, nfields, stream=None)
            "lmvd_inverse_transform_noalloc")
 
 
+def lmvd_checked_build():
+    """1 if the loaded library is the index-checked build (liblmvd_check.so), else 0."""
+    return int(_lib.lmvd_checked_build())
+
+
+def lmvd_rate_probe(op, iters=20000, stream=None):
+    """Operations per second of op (0 FP64 FMA, 1 FP64 add, 2 FP64 multiply, 3 FP32 FMA) on the current device."""
+    out = ctypes.c_double(0.0)
+    st = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
+    _check(_lib.lmvd_rate_probe(int(op), int(iters), ctypes.byref(out), st), "lmvd_rate_probe")
+    return out.value
+
+
 def lmvd_state_bytes(h):
     return int(_lib.lmvd_state_bytes(h))
 
@@ -246,13 +263,15 @@ def lmvd_diagnostics_enable(h, on=True):
 
 
 def lmvd_diagnostics(h):
-    """dict(substage, mass_residual, fp_changes=[...]) of the last substage's record."""
-    buf = (ctypes.c_double * 18)()
-    n = _lib.lmvd_diagnostics(h, buf, 18)
+    """dict(substage, mass_residual, fp_changes=[...], kinetic_energy, max_momentum, mean_m2c_y0) of the last
+    substage's record."""
+    buf = (ctypes.c_double * 24)()
+    n = _lib.lmvd_diagnostics(h, buf, 24)
     if n < 0:
         _check(n, "lmvd_diagnostics")
-    vals = list(buf)[:min(n, 18)]
-    return dict(substage=int(vals[0]), mass_residual=vals[1], fp_changes=vals[2:])
+    vals = list(buf)[:min(n, 24)]
+    return dict(substage=int(vals[0]), mass_residual=vals[1], fp_changes=vals[2:-3], kinetic_energy=vals[-3],
+                max_momentum=vals[-2], mean_m2c_y0=vals[-1])
 
 
 def lmvd_device_bytes(h):

@@ -107,6 +107,11 @@ def test_host_side_argument_checks_without_gpu(lib):
     assert L.lmvd_inverse_transform_noalloc(8, 9, 8, None, fake, 1, None) == -1       # NULL spec
     assert L.lmvd_inverse_transform_noalloc(8, 9, 8, fake, fake, -1, None) == -1      # nfields < 0
     assert L.lmvd_inverse_transform_noalloc(10, 9, 8, fake, fake, 1, None) == -5      # 3nx/2 = 15 = 3 * 5
+    assert L.lmvd_inverse_transform_noalloc(4, 70000, 4, fake, fake, 1, None) == -1   # ny > 65535 (fits the array)
+    out = ctypes.c_double(0.0)
+    assert L.lmvd_rate_probe(0, 10, None, None) == -1                                  # NULL output
+    assert L.lmvd_rate_probe(4, 10, ctypes.byref(out), None) == -1                     # unknown op
+    assert L.lmvd_rate_probe(0, 0, ctypes.byref(out), None) == -1                      # no iterations
     assert L.lmvd_df64_convert(None, None, None, None, None, None, 0, None) == 0      # nothing to do
     assert L.lmvd_df64_convert(None, None, None, None, None, None, 4, None) == -1
 
@@ -119,3 +124,15 @@ def test_every_exported_function_has_a_ctypes_signature(lib):
         assert fn.argtypes is not None, name
         if name != "lmvd_destroy":
             assert fn.restype is not None, name
+
+
+def test_checked_build_reports_itself(lib):
+    """liblmvd.so is the normal build; liblmvd_check.so (built beside it) has the kernels' index checks."""
+    import ctypes
+    import os
+    assert lib._lib.lmvd_checked_build() == 0
+    chk = ctypes.CDLL(os.path.join(os.path.dirname(lib.LIB_PATH), "liblmvd_check.so"))
+    chk.lmvd_checked_build.restype = ctypes.c_int
+    assert chk.lmvd_checked_build() == 1
+    chk.lmvd_strerror.restype = ctypes.c_char_p
+    assert b"bounds" in chk.lmvd_strerror(-7)

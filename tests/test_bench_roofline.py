@@ -31,3 +31,15 @@ def test_traffic_is_null_without_a_matching_capture():
     assert bench.roofline_of(prof, 200.0, 0, (512, 513, 512))["traffic"] is None      # no capture of this class
     prof = {"fft_x_inverse": (100.0, 5.0, 1e13, 5e10)}
     assert bench.roofline_of(prof, 200.0, 0, (256, 257, 256))["traffic"] is None      # other transform length
+
+
+def test_measured_rates_set_the_peaks():
+    """With the probe's rates, the FP64 peak is 2 flop x the FP64 FMA rate and the double-float one the FP32
+    FMA rate / 10 instructions per classic flop."""
+    import bench
+    prof = {"fft_x_inverse": (200.0, 10.0, 1.5e14, 9.0e10)}
+    rates = {"fp64_fma": 6.0e11, "fp64_add": 5.0e11, "fp64_mul": 5.0e11, "fp32_fma": 4.0e13}
+    r = bench.roofline_of(prof, 400.0, 0, (512, 513, 512), rates)
+    assert r["peak"] == pytest.approx(1.2) and "measured" in r["peak_note"]
+    rd = bench.roofline_of(prof, 400.0, 1, (512, 513, 512), rates)
+    assert rd["peak"] == pytest.approx(4.0) and rd["frac"] == pytest.approx(rd["achieved"] / 4.0)

@@ -6,6 +6,8 @@
 * The diagnostics record (lmvd_diagnostics) matches the oracle: the relative change of each fixed-point
   application |dz/dt^{k+1} - dz/dt^k| / |dz/dt^{k+1}| is the oracle's fp_residuals (Sec. 3.1), and the
   relative mass residual of m^c is at rounding level (Sec. 4.2, exact D*).
+* The record's kinetic energy, max |m| and bottom value of <m2^c> match the same quantities formed from the
+  oracle's fields, and take their closed-form values for a uniform stream (KE = U^2 / 2 times the volume).
 * At density ratio 100 with a sharp interface the fixed point does not converge (the oracle shows
   relative changes above 1 throughout); lmvd_synchronize returns LMVD_ERR_FP_DIVERGED. At the paper's
   density ratios it stays clean.
@@ -66,6 +68,61 @@ def test_diagnostics_match_oracle(L):
         assert len(d["fp_changes"]) == cfg.kf
         for g, o in zip(d["fp_changes"], S.fp_residuals):
             assert abs(g - o) <= 1e-3 * o + 1e-11, (g, o)
+    ctx.close()
+
+
+def _oracle_energy(S):
+    """(1/2) integral of |m^d + m^c|^2 / rho dV and max |m| from the oracle's fields of its last substage."""
+    from oracle.lmvd import _ax0
+    op, cfg = S.op, S.cfg
+    m1c, m2c, m3c = S.trace["mc"]
+    mcp = (op.phys(_ax0(op.Bg[0], m1c)), op.phys(_ax0(op.Sg0, m2c)), op.phys(_ax0(op.Bg[0], m3c)))
+    m2 = sum((S.md_phys[i] + mcp[i]) ** 2 for i in range(3))
+    b = op.basis
+    integral = (b.t[cfg.p:cfg.p + cfg.ny] - b.t[:cfg.ny]) / cfg.p          # integral of each B_j
+    wq = np.linalg.solve(b.Bg[0].T, integral)                             # weights at the Greville points
+    plane = np.mean(0.5 * m2 / S.rho, axis=(1, 2))
+    return cfg.lx * cfg.lz * float(wq @ plane), float(np.sqrt(m2.max()))
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_diagnostics_energy_and_wall_flux_match_oracle(L, precision):
+    from _pairs import make_pair, to_torch
+    S, ctx, st, cfg = make_pair(L, "rt32", precision=precision)
+    L.lmvd_diagnostics_enable(ctx.h, True)
+    S.set_state(**st)
+    ctx.set_state(to_torch(st))
+    for s in range(3):
+        S.advance_substage()
+        ctx.advance_substage()
+        d = L.lmvd_diagnostics(ctx.h)
+        ke, mmax = _oracle_energy(S)
+        mc2 = S.trace["mc"][1][0, 0, 0].real
+        print(s, d["kinetic_energy"], ke, d["max_momentum"], mmax, d["mean_m2c_y0"], mc2)
+        assert abs(d["kinetic_energy"] - ke) <= 1e-10 * ke
+        assert abs(d["max_momentum"] - mmax) <= 1e-10 * mmax
+        assert abs(d["mean_m2c_y0"] - mc2) <= 1e-9 * abs(mc2) + 1e-20
+    ctx.close()
+
+
+def test_diagnostics_uniform_stream_closed_form(L):
+    """Uniform density, <m1> = U, <m3> = W (potential matching: Neumann rows keep them): KE = (U^2 + W^2)/2
+    times lx lz (y1 - y0), max |m| = sqrt(U^2 + W^2), no mass flux (to rounding)."""
+    from _pairs import make_pair, to_torch
+    S, ctx, st, cfg = make_pair(L, "rt32", bc="potential")
+    st = {k: np.zeros_like(v) for k, v in st.items()}
+    st["z"][:, 0, 0] = 1.0                     # z = 1 everywhere: rho = rho_h = 1 exactly (Sec. 5 EOS)
+    U, W = 0.3, -0.2
+    st["mm1"][:] = U
+    st["mm3"][:] = W
+    L.lmvd_diagnostics_enable(ctx.h, True)
+    ctx.set_state(to_torch(st))
+    ctx.advance_substage()
+    d = L.lmvd_diagnostics(ctx.h)
+    vol = cfg.lx * cfg.lz * (cfg.y1 - cfg.y0)
+    assert abs(d["kinetic_energy"] - 0.5 * (U * U + W * W) * vol) <= 1e-13 * vol
+    assert abs(d["max_momentum"] - np.hypot(U, W)) <= 1e-14
+    assert abs(d["mean_m2c_y0"]) <= 1e-14      # z is 1 up to the rounding of the spline sum
     ctx.close()
 
 
