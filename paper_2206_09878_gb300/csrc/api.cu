@@ -404,21 +404,27 @@ void physical_pass_1(Ctx& c, double* const* zp = nullptr) {
 // a: where zdot lands on the physical grid; b: where m^c lands (work fields by default).
 void mc_from_zdot(Ctx& c, double* a = nullptr, double* const* b = nullptr) {
   const size_t n = (size_t)c.g.ny * c.g.P;
+  const bool keep_a = a != nullptr;  // the adjoint's tape keeps dz/dt on the grid: separate product pass
   if (!a) a = c.pw[0];
   double* bb[3] = {c.pw[0], c.pw[1], c.pw[2]};
   if (b)
     for (int f = 0; f < 3; ++f) bb[f] = b[f];
   eval_jobs(c, {EvalJob{c.B0g, c.zdot, c.sv[0], 0}});
-  {
-    cd* in[1] = {c.sv[0]};
-    double* out[1] = {a};
-    fft_inverse(c, in, out, 1);
+  if (!keep_a) {
+    // rho_t = f' dz/dt formed in the epilogue of the inverse x-pass (dz/dt on the grid is not stored)
+    fft_inverse_mul(c, c.sv[0], c.pw[1], c.fprime);
+  } else {
+    {
+      cd* in[1] = {c.sv[0]};
+      double* out[1] = {a};
+      fft_inverse(c, in, out, 1);
+    }
+    if (c.cfg.precision == 1)
+      LMVD_LAUNCH(c, KC_PRODUCTS, 1.0 * n, 24.0 * n, k_product_rt_df, elem_blocks(n), 256, 0, n, c.fprime, a,
+                  c.pw[1]);
+    else
+      LMVD_LAUNCH(c, KC_PRODUCTS, 1.0 * n, 24.0 * n, k_product_rt, elem_blocks(n), 256, 0, n, c.fprime, a, c.pw[1]);
   }
-  if (c.cfg.precision == 1)
-    LMVD_LAUNCH(c, KC_PRODUCTS, 1.0 * n, 24.0 * n, k_product_rt_df, elem_blocks(n), 256, 0, n, c.fprime, a,
-                c.pw[1]);
-  else
-    LMVD_LAUNCH(c, KC_PRODUCTS, 1.0 * n, 24.0 * n, k_product_rt, elem_blocks(n), 256, 0, n, c.fprime, a, c.pw[1]);
   {
     double* in[1] = {c.pw[1]};
     cd* out[1] = {c.sv[1]};
@@ -445,16 +451,10 @@ void fp_apply(Ctx& c, double* a = nullptr, double* const* b = nullptr) {
   double* bb[3] = {c.pw[0], c.pw[1], c.pw[2]};
   if (b)
     for (int f = 0; f < 3; ++f) bb[f] = b[f];
-  const size_t n = (size_t)c.g.ny * c.g.P;
-  if (c.cfg.precision == 1)
-    LMVD_LAUNCH(c, KC_PRODUCTS, 6.0 * n, 56.0 * n, k_product_L_df, elem_blocks(n), 256, 0, n, c.w[0], c.w[1], c.w[2],
-                bb[0], bb[1], bb[2], c.pw[3]);
-  else
-    LMVD_LAUNCH(c, KC_PRODUCTS, 6.0 * n, 56.0 * n, k_product_L, elem_blocks(n), 256, 0, n, c.w[0], c.w[1], c.w[2],
-                bb[0], bb[1], bb[2], c.pw[3]);
-  double* in[1] = {c.pw[3]};
-  cd* out[1] = {c.sv[3]};
-  fft_forward(c, in, out, 1);
+  // the tail -(grad z / rho) . m^c formed in the prologue of the forward x-pass
+  const double* w[3] = {c.w[0], c.w[1], c.w[2]};
+  const double* m[3] = {bb[0], bb[1], bb[2]};
+  fft_forward_dot3(c, w, m, c.sv[3]);
   solve_interp(c, {SolveJob{c.sv[3], c.Rz, c.zdot}}, c.lu_interp);
 }
 

@@ -72,6 +72,9 @@ struct FT<cd> {
   __device__ static R re(cd a) { return a.re; }
   __device__ static R im(cd a) { return a.im; }
   __device__ static R rzero() { return 0.0; }
+  __device__ static R rmul(R a, R b) { return a * b; }
+  // -(w1 m1 + w2 m2 + w3 m3), the expression of k_product_L
+  __device__ static R dot3neg(R w1, R m1, R w2, R m2, R w3, R m3) { return -(w1 * m1 + w2 * m2 + w3 * m3); }
 };
 
 template <>
@@ -107,6 +110,11 @@ struct FT<cdf> {
   __device__ static R re(cdf a) { return a.re; }
   __device__ static R im(cdf a) { return a.im; }
   __device__ static R rzero() { return df{0.f, 0.f}; }
+  __device__ static R rmul(R a, R b) { return dmul(a, b); }
+  // -(w1 m1 + w2 m2 + w3 m3), the arithmetic of k_product_L_df
+  __device__ static R dot3neg(R w1, R m1, R w2, R m2, R w3, R m3) {
+    return dneg(dadd(ddot2(w1, m1, w2, m2), dmul(w3, m3)));
+  }
 };
 
 // One radix-R Stockham stage, in place in shared memory. The transform of length n is shared by
@@ -223,8 +231,12 @@ __global__ void __launch_bounds__(FFT_CTA_Z, FFT_MIN_CTAS_Z) k_fft_z_inv(FFTPlan
 }
 
 // ---------------------------------------------------------------- inverse x-pass (c2r, 2 rows per transform)
-template <class C, int EPT>
-__global__ void __launch_bounds__(FFT_CTA_X, FFT_MIN_CTAS_X) k_fft_x_inv(FFTPlan pl, Grid g, const C* T, size_t tstride, FieldsRW out) {
+// With MUL the epilogue stores w * phys instead of phys (w: a physical field of the same layout, one for all
+// fields of the launch): the product f'(z) dz/dt of the fixed point (Sec. 4.3) formed as the transform is
+// written, so neither dz/dt on the grid nor a separate product pass is needed.
+template <class C, int EPT, bool MUL>
+__device__ __forceinline__ void x_inv_body(const FFTPlan& pl, const Grid& g, const C* T, size_t tstride,
+                                           const FieldsRW& out, const void* wmul) {
   using F = FT<C>;
   using R = typename F::R;
   extern __shared__ __align__(16) unsigned char sm_raw[];
@@ -260,14 +272,37 @@ __global__ void __launch_bounds__(FFT_CTA_X, FFT_MIN_CTAS_X) k_fft_x_inv(FFTPlan
     if (za >= pz) continue;
     if (!LMVD_IN((size_t)za * px + x, g.P) || !LMVD_IN(bb * ld + x, batch * ld)) continue;
     const C v = res[bb * ld + x];
-    dst[(size_t)za * px + x] = F::re(v);
-    if (zb < pz) dst[(size_t)zb * px + x] = F::im(v);
+    if (MUL) {
+      const R* w = reinterpret_cast<const R*>(wmul) + (size_t)j * g.P;
+      dst[(size_t)za * px + x] = F::rmul(w[(size_t)za * px + x], F::re(v));
+      if (zb < pz) dst[(size_t)zb * px + x] = F::rmul(w[(size_t)zb * px + x], F::im(v));
+    } else {
+      dst[(size_t)za * px + x] = F::re(v);
+      if (zb < pz) dst[(size_t)zb * px + x] = F::im(v);
+    }
   }
+}
+template <class C, int EPT>
+__global__ void __launch_bounds__(FFT_CTA_X, FFT_MIN_CTAS_X) k_fft_x_inv(FFTPlan pl, Grid g, const C* T, size_t tstride, FieldsRW out) {
+  x_inv_body<C, EPT, false>(pl, g, T, tstride, out, nullptr);
+}
+template <class C, int EPT>
+__global__ void __launch_bounds__(FFT_CTA_X, FFT_MIN_CTAS_X) k_fft_x_inv_mul(FFTPlan pl, Grid g, const C* T, size_t tstride, FieldsRW out,
+                                                                             const void* wmul) {
+  x_inv_body<C, EPT, true>(pl, g, T, tstride, out, wmul);
 }
 
 // ---------------------------------------------------------------- forward x-pass (r2c, 2 rows per transform)
-template <class C, int EPT>
-__global__ void __launch_bounds__(FFT_CTA_X, FFT_MIN_CTAS_X) k_fft_x_fwd(FFTPlan pl, Grid g, FieldsRC in, C* T, size_t tstride) {
+// With DOT3 the load prologue forms -(w1 m1 + w2 m2 + w3 m3) from six physical fields instead of reading
+// one (d: w[0..2], m[0..2]; one launch, one field): the tail -(1/rho) grad z . m^c of L (Sec. 4.3) formed as
+// the transform reads it, so no product pass and no product field are needed.
+struct Dot3 {
+  const void* w[3];
+  const void* m[3];
+};
+template <class C, int EPT, bool DOT3>
+__device__ __forceinline__ void x_fwd_body(const FFTPlan& pl, const Grid& g, const FieldsRC& in, C* T, size_t tstride,
+                                           const Dot3& d) {
   using F = FT<C>;
   using R = typename F::R;
   extern __shared__ __align__(16) unsigned char sm_raw[];
@@ -281,8 +316,24 @@ __global__ void __launch_bounds__(FFT_CTA_X, FFT_MIN_CTAS_X) k_fft_x_fwd(FFTPlan
     const int za = 2 * (pr0 + bb), zb = za + 1;
     R va = F::rzero(), vb = F::rzero();
     if (za < pz && LMVD_IN((size_t)za * px + x, g.P)) {
-      va = src[(size_t)za * px + x];
-      if (zb < pz) vb = src[(size_t)zb * px + x];
+      if (DOT3) {
+        const size_t plane = (size_t)j * g.P;
+        const R* w0 = reinterpret_cast<const R*>(d.w[0]) + plane;
+        const R* w1 = reinterpret_cast<const R*>(d.w[1]) + plane;
+        const R* w2 = reinterpret_cast<const R*>(d.w[2]) + plane;
+        const R* m0 = reinterpret_cast<const R*>(d.m[0]) + plane;
+        const R* m1 = reinterpret_cast<const R*>(d.m[1]) + plane;
+        const R* m2 = reinterpret_cast<const R*>(d.m[2]) + plane;
+        size_t o = (size_t)za * px + x;
+        va = F::dot3neg(w0[o], m0[o], w1[o], m1[o], w2[o], m2[o]);
+        if (zb < pz) {
+          o += px;
+          vb = F::dot3neg(w0[o], m0[o], w1[o], m1[o], w2[o], m2[o]);
+        }
+      } else {
+        va = src[(size_t)za * px + x];
+        if (zb < pz) vb = src[(size_t)zb * px + x];
+      }
     }
     if (LMVD_IN(bb * ld + x, batch * ld)) a[bb * ld + x] = F::make(va, vb);
   }
@@ -300,6 +351,14 @@ __global__ void __launch_bounds__(FFT_CTA_X, FFT_MIN_CTAS_X) k_fft_x_fwd(FFTPlan
     dst[(size_t)za * h + k] = F::half(F::add(yk, ym));
     if (zb < pz) dst[(size_t)zb * h + k] = F::neg(F::ti(F::half(F::sub(yk, ym))));  // (yk - ym) / (2 i)
   }
+}
+template <class C, int EPT>
+__global__ void __launch_bounds__(FFT_CTA_X, FFT_MIN_CTAS_X) k_fft_x_fwd(FFTPlan pl, Grid g, FieldsRC in, C* T, size_t tstride) {
+  x_fwd_body<C, EPT, false>(pl, g, in, T, tstride, Dot3{});
+}
+template <class C, int EPT>
+__global__ void __launch_bounds__(FFT_CTA_X, FFT_MIN_CTAS_X) k_fft_x_fwd_dot3(FFTPlan pl, Grid g, C* T, size_t tstride, Dot3 d) {
+  x_fwd_body<C, EPT, true>(pl, g, FieldsRC{}, T, tstride, d);
 }
 
 // ---------------------------------------------------------------- forward z-pass (truncate, scale)
@@ -367,7 +426,9 @@ static int set_smem_e(int sx, int sz) {
   if (cudaFuncSetAttribute(k_fft_z_inv<C, EPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, sz) != cudaSuccess ||
       cudaFuncSetAttribute(k_fft_z_fwd<C, EPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, sz) != cudaSuccess ||
       cudaFuncSetAttribute(k_fft_x_inv<C, EPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, sx) != cudaSuccess ||
-      cudaFuncSetAttribute(k_fft_x_fwd<C, EPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, sx) != cudaSuccess)
+      cudaFuncSetAttribute(k_fft_x_fwd<C, EPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, sx) != cudaSuccess ||
+      cudaFuncSetAttribute(k_fft_x_inv_mul<C, EPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, sx) != cudaSuccess ||
+      cudaFuncSetAttribute(k_fft_x_fwd_dot3<C, EPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, sx) != cudaSuccess)
     return LMVD_ERR_CUDA;
   return LMVD_OK;
 }
@@ -417,7 +478,7 @@ static inline unsigned cdiv(unsigned a, unsigned b) { return (a + b - 1) / b; }
 static inline double fft_flops(double n) { return 5.0 * n * std::log2(n); }
 
 template <class C>
-static void inverse_t(Ctx& c, cd* const* in, void* const* out, int nf) {
+static void inverse_t(Ctx& c, cd* const* in, void* const* out, int nf, const void* wmul = nullptr) {
   const Grid& g = c.g;
   const size_t tstride = (size_t)g.ny * g.pz * (g.nx / 2);
   C* T = reinterpret_cast<C*>(c.tbuf);
@@ -438,12 +499,21 @@ static void inverse_t(Ctx& c, cd* const* in, void* const* out, int nf) {
       LMVD_LAUNCH(c, KC_FFT_Z_INV, n * ny * h * fft_flops(pz), n * ny * h * 16.0 * ((g.nz - 1) + pz),
                   (k_fft_z_inv<C, 6>), gz, threads(c.fz), smem_bytes(c.fz), c.fz, g, fi, T, tstride);
     dim3 gx(cdiv(cdiv(g.pz, 2), c.fx.batch), g.ny, n);
-    if (c.fx.ept == 12)
-      LMVD_LAUNCH(c, KC_FFT_X_INV, n * ny * ((g.pz + 1) / 2) * fft_flops(px), n * ny * pz * (16.0 * h + 8.0 * px),
-                  (k_fft_x_inv<C, 12>), gx, threads(c.fx), smem_bytes(c.fx), c.fx, g, T, tstride, fo);
-    else
-      LMVD_LAUNCH(c, KC_FFT_X_INV, n * ny * ((g.pz + 1) / 2) * fft_flops(px), n * ny * pz * (16.0 * h + 8.0 * px),
-                  (k_fft_x_inv<C, 6>), gx, threads(c.fx), smem_bytes(c.fx), c.fx, g, T, tstride, fo);
+    const double xfl = n * ny * ((g.pz + 1) / 2) * fft_flops(px), xby = n * ny * pz * (16.0 * h + 8.0 * px);
+    if (wmul) {  // the product with w in the epilogue: one more physical field read, one multiply per point
+      if (c.fx.ept == 12)
+        LMVD_LAUNCH(c, KC_FFT_X_INV, xfl + n * ny * pz * px, xby + n * ny * pz * 8.0 * px, (k_fft_x_inv_mul<C, 12>),
+                    gx, threads(c.fx), smem_bytes(c.fx), c.fx, g, T, tstride, fo, wmul);
+      else
+        LMVD_LAUNCH(c, KC_FFT_X_INV, xfl + n * ny * pz * px, xby + n * ny * pz * 8.0 * px, (k_fft_x_inv_mul<C, 6>),
+                    gx, threads(c.fx), smem_bytes(c.fx), c.fx, g, T, tstride, fo, wmul);
+    } else if (c.fx.ept == 12) {
+      LMVD_LAUNCH(c, KC_FFT_X_INV, xfl, xby, (k_fft_x_inv<C, 12>), gx, threads(c.fx), smem_bytes(c.fx), c.fx, g, T,
+                  tstride, fo);
+    } else {
+      LMVD_LAUNCH(c, KC_FFT_X_INV, xfl, xby, (k_fft_x_inv<C, 6>), gx, threads(c.fx), smem_bytes(c.fx), c.fx, g, T,
+                  tstride, fo);
+    }
   }
 }
 
@@ -476,6 +546,49 @@ static void forward_t(Ctx& c, void* const* in, cd* const* out, int nf) {
       LMVD_LAUNCH(c, KC_FFT_Z_FWD, n * ny * h * fft_flops(pz), n * ny * 16.0 * (pz * h + (double)g.nz * g.nxh),
                   (k_fft_z_fwd<C, 6>), gz, threads(c.fz), smem_bytes(c.fz), c.fz, g, T, tstride, fo);
   }
+}
+
+// forward transform of -(w1 m1 + w2 m2 + w3 m3), formed in the x-pass prologue, into one spectral field
+template <class C>
+static void forward_dot3_t(Ctx& c, const double* const* w, const double* const* m, cd* out) {
+  const Grid& g = c.g;
+  const size_t tstride = (size_t)g.ny * g.pz * (g.nx / 2);
+  C* T = reinterpret_cast<C*>(c.tbuf);
+  Dot3 d{};
+  for (int f = 0; f < 3; ++f) {
+    d.w[f] = w[f];
+    d.m[f] = m[f];
+  }
+  FieldsW fo{};
+  fo.p[0] = out;
+  const double h = g.nx / 2, ny = g.ny, pz = g.pz, px = g.px;
+  dim3 gx(cdiv(cdiv(g.pz, 2), c.fx.batch), g.ny, 1);
+  const double xfl = ny * ((g.pz + 1) / 2) * fft_flops(px) + 6.0 * ny * pz * px, xby = ny * pz * (16.0 * h + 48.0 * px);
+  if (c.fx.ept == 12)
+    LMVD_LAUNCH(c, KC_FFT_X_FWD, xfl, xby, (k_fft_x_fwd_dot3<C, 12>), gx, threads(c.fx), smem_bytes(c.fx), c.fx, g, T,
+                tstride, d);
+  else
+    LMVD_LAUNCH(c, KC_FFT_X_FWD, xfl, xby, (k_fft_x_fwd_dot3<C, 6>), gx, threads(c.fx), smem_bytes(c.fx), c.fx, g, T,
+                tstride, d);
+  dim3 gz(cdiv(g.nx / 2 + 1, c.fz.batch), g.ny, 1);
+  if (c.fz.ept == 12)
+    LMVD_LAUNCH(c, KC_FFT_Z_FWD, ny * h * fft_flops(pz), ny * 16.0 * (pz * h + (double)g.nz * g.nxh),
+                (k_fft_z_fwd<C, 12>), gz, threads(c.fz), smem_bytes(c.fz), c.fz, g, T, tstride, fo);
+  else
+    LMVD_LAUNCH(c, KC_FFT_Z_FWD, ny * h * fft_flops(pz), ny * 16.0 * (pz * h + (double)g.nz * g.nxh),
+                (k_fft_z_fwd<C, 6>), gz, threads(c.fz), smem_bytes(c.fz), c.fz, g, T, tstride, fo);
+}
+
+void fft_inverse_mul(Ctx& c, cd* in, double* out, const double* w) {
+  cd* i[1] = {in};
+  void* o[1] = {out};
+  if (c.cfg.precision == 1) inverse_t<cdf>(c, i, o, 1, w);
+  else inverse_t<cd>(c, i, o, 1, w);
+}
+
+void fft_forward_dot3(Ctx& c, const double* const* w, const double* const* m, cd* out) {
+  if (c.cfg.precision == 1) forward_dot3_t<cdf>(c, w, m, out);
+  else forward_dot3_t<cd>(c, w, m, out);
 }
 
 void fft_inverse_as(Ctx& c, cd* const* in, double* const* out, int nf, int precision) {

@@ -328,5 +328,10 @@ void fft_forward(Ctx& c, double* const* in, cd* const* out, int nf);
 // the same with an explicit arithmetic (0: complex double, 1: double-float), nf <= 64
 void fft_inverse_as(Ctx& c, cd* const* in, double* const* out, int nf, int precision);
 void fft_forward_as(Ctx& c, double* const* in, cd* const* out, int nf, int precision);
+// the fixed point's products formed inside the x-passes (Sec. 4.3): inverse transform of one field whose
+// x-pass stores w * phys (rho_t = f'(z) dz/dt), and forward transform of -(w1 m1 + w2 m2 + w3 m3) formed
+// in the x-pass prologue (the tail of L); w, m: physical fields in the arithmetic of the precision
+void fft_inverse_mul(Ctx& c, cd* in, double* out, const double* w);
+void fft_forward_dot3(Ctx& c, const double* const* w, const double* const* m, cd* out);
 
 }  // namespace lmvd
