@@ -320,16 +320,14 @@ void eval_jobs(Ctx& c, std::initializer_list<EvalJob> jobs) {
     rows += 2.0 * j.B.rows;
     fl += 4.0 * j.B.rows * j.B.w;
   }
-  int maxrows = 0;
-  bool acc = false;
+  int maxrows = 0, maxw = 0;
   for (int q = 0; q < n; ++q) {
     maxrows = std::max(maxrows, ej.j[q].B.rows);
-    acc = acc || ej.j[q].acc;
+    maxw = std::max(maxw, ej.j[q].B.w);
   }
-  int maxw = 0;
-  for (int q = 0; q < n; ++q) maxw = std::max(maxw, ej.j[q].B.w);
-  // the precision path evaluates the values that feed its transforms in double-float
-  if (c.cfg.precision == 1 && !acc && maxw >= 4 && maxw <= 9) {
+  // the precision path evaluates the values that feed its transforms in double-float, stored as pairs for
+  // its inverse transforms (fft_inverse); its jobs never accumulate
+  if (c.cfg.precision == 1) {
     const dim3 grid(mode_blocks(c.g), n, row_chunks(c.g, maxrows));
     LMVD_LAUNCH_CALL(c, KC_EVAL, fl * c.g.M, 16.0 * rows * c.g.M,
                      launch_eval_df(maxw, grid, TPB_MODE, c.stream, c.g, ej));

@@ -20,6 +20,7 @@
 #include <cmath>
 #include <cstring>
 #include <mutex>
+#include <type_traits>
 
 #include "df64.h"
 #include "lmvd_internal.h"
@@ -200,7 +201,9 @@ constexpr int FFT_CTA_X = 128, FFT_MIN_CTAS_X = 6, FFT_CTA_Z = 256, FFT_MIN_CTAS
 
 // ---------------------------------------------------------------- inverse z-pass
 // in: spectral value fields [ny][nz][nxh] (complex double); T: [f][ny][pz][nx/2] of C
-template <class C, int EPT>
+// IN_DF (double-float arithmetic only): the inputs already hold double-float pairs (the precision path's
+// evaluations store them so), read without conversion.
+template <class C, int EPT, bool IN_DF = false>
 __global__ void __launch_bounds__(FFT_CTA_Z, FFT_MIN_CTAS_Z) k_fft_z_inv(FFTPlan pl, Grid g, FieldsC in, C* T, size_t tstride) {
   using F = FT<C>;
   extern __shared__ __align__(16) unsigned char sm_raw[];
@@ -215,8 +218,10 @@ __global__ void __launch_bounds__(FFT_CTA_Z, FFT_MIN_CTAS_Z) k_fft_z_inv(FFTPlan
     const int jz = idx / batch, bb = idx - jz * batch, kx = kx0 + bb;
     if (kx < h && jz != nz / 2) {
       const int pos = jz < nz / 2 ? jz : pz - nz + jz;
-      if (LMVD_IN(bb * ld + pos, batch * ld) && LMVD_IN((size_t)jz * g.nxh + kx, g.M))
-        a[bb * ld + pos] = F::from_spec(src[(size_t)jz * g.nxh + kx]);
+      if (LMVD_IN(bb * ld + pos, batch * ld) && LMVD_IN((size_t)jz * g.nxh + kx, g.M)) {
+        if constexpr (IN_DF) a[bb * ld + pos] = reinterpret_cast<const C*>(src)[(size_t)jz * g.nxh + kx];
+        else a[bb * ld + pos] = F::from_spec(src[(size_t)jz * g.nxh + kx]);
+      }
     }
   }
   __syncthreads();
@@ -438,6 +443,9 @@ static int set_smem(const FFTPlan& fx, const FFTPlan& fz) {
   const int sx = (int)smem_bytes(fx), sz = (int)smem_bytes(fz);
   int e = set_smem_e<C, 12>(sx, sz);
   if (!e) e = set_smem_e<C, 6>(sx, sz);
+  if (!e && (cudaFuncSetAttribute(k_fft_z_inv<cdf, 12, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sz) != cudaSuccess ||
+             cudaFuncSetAttribute(k_fft_z_inv<cdf, 6, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sz) != cudaSuccess))
+    e = LMVD_ERR_CUDA;
   return e;
 }
 
@@ -478,7 +486,7 @@ static inline unsigned cdiv(unsigned a, unsigned b) { return (a + b - 1) / b; }
 static inline double fft_flops(double n) { return 5.0 * n * std::log2(n); }
 
 template <class C>
-static void inverse_t(Ctx& c, cd* const* in, void* const* out, int nf, const void* wmul = nullptr) {
+static void inverse_t(Ctx& c, cd* const* in, void* const* out, int nf, const void* wmul = nullptr, bool in_df = false) {
   const Grid& g = c.g;
   const size_t tstride = (size_t)g.ny * g.pz * (g.nx / 2);
   C* T = reinterpret_cast<C*>(c.tbuf);
@@ -492,12 +500,20 @@ static void inverse_t(Ctx& c, cd* const* in, void* const* out, int nf, const voi
     }
     const double h = g.nx / 2, ny = g.ny, pz = g.pz, px = g.px;
     dim3 gz(cdiv(g.nx / 2, c.fz.batch), g.ny, n);
-    if (c.fz.ept == 12)
-      LMVD_LAUNCH(c, KC_FFT_Z_INV, n * ny * h * fft_flops(pz), n * ny * h * 16.0 * ((g.nz - 1) + pz),
-                  (k_fft_z_inv<C, 12>), gz, threads(c.fz), smem_bytes(c.fz), c.fz, g, fi, T, tstride);
+    const double zfl = n * ny * h * fft_flops(pz), zby = n * ny * h * 16.0 * ((g.nz - 1) + pz);
+    // double-float inputs only exist for the double-float arithmetic
+    if (in_df && c.fz.ept == 12)
+      LMVD_LAUNCH(c, KC_FFT_Z_INV, zfl, zby, (k_fft_z_inv<C, 12, std::is_same<C, cdf>::value>), gz, threads(c.fz),
+                  smem_bytes(c.fz), c.fz, g, fi, T, tstride);
+    else if (in_df)
+      LMVD_LAUNCH(c, KC_FFT_Z_INV, zfl, zby, (k_fft_z_inv<C, 6, std::is_same<C, cdf>::value>), gz, threads(c.fz),
+                  smem_bytes(c.fz), c.fz, g, fi, T, tstride);
+    else if (c.fz.ept == 12)
+      LMVD_LAUNCH(c, KC_FFT_Z_INV, zfl, zby, (k_fft_z_inv<C, 12>), gz, threads(c.fz), smem_bytes(c.fz), c.fz, g, fi,
+                  T, tstride);
     else
-      LMVD_LAUNCH(c, KC_FFT_Z_INV, n * ny * h * fft_flops(pz), n * ny * h * 16.0 * ((g.nz - 1) + pz),
-                  (k_fft_z_inv<C, 6>), gz, threads(c.fz), smem_bytes(c.fz), c.fz, g, fi, T, tstride);
+      LMVD_LAUNCH(c, KC_FFT_Z_INV, zfl, zby, (k_fft_z_inv<C, 6>), gz, threads(c.fz), smem_bytes(c.fz), c.fz, g, fi,
+                  T, tstride);
     dim3 gx(cdiv(cdiv(g.pz, 2), c.fx.batch), g.ny, n);
     const double xfl = n * ny * ((g.pz + 1) / 2) * fft_flops(px), xby = n * ny * pz * (16.0 * h + 8.0 * px);
     if (wmul) {  // the product with w in the epilogue: one more physical field read, one multiply per point
@@ -582,7 +598,7 @@ static void forward_dot3_t(Ctx& c, const double* const* w, const double* const* 
 void fft_inverse_mul(Ctx& c, cd* in, double* out, const double* w) {
   cd* i[1] = {in};
   void* o[1] = {out};
-  if (c.cfg.precision == 1) inverse_t<cdf>(c, i, o, 1, w);
+  if (c.cfg.precision == 1) inverse_t<cdf>(c, i, o, 1, w, true);
   else inverse_t<cd>(c, i, o, 1, w);
 }
 
@@ -605,7 +621,15 @@ void fft_forward_as(Ctx& c, double* const* in, cd* const* out, int nf, int preci
   else forward_t<cd>(c, i, out, nf);
 }
 
-void fft_inverse(Ctx& c, cd* const* in, double* const* out, int nf) { fft_inverse_as(c, in, out, nf, c.cfg.precision); }
+void fft_inverse(Ctx& c, cd* const* in, double* const* out, int nf) {
+  if (c.cfg.precision == 1) {  // the substage's inputs come from the double-float evaluations
+    void* o[64];
+    for (int f = 0; f < nf; ++f) o[f] = out[f];
+    inverse_t<cdf>(c, in, o, nf, nullptr, true);
+  } else {
+    fft_inverse_as(c, in, out, nf, 0);
+  }
+}
 
 void fft_forward(Ctx& c, double* const* in, cd* const* out, int nf) { fft_forward_as(c, in, out, nf, c.cfg.precision); }
 

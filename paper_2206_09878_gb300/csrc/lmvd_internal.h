@@ -321,7 +321,8 @@ void prof_end(Ctx& c, int cls, cudaEvent_t a, double flops, double bytes);
 
 // ---------------------------------------------------------------- launchers (defined in .cu files)
 int fft_prepare(Ctx& c);                       // plans, twiddles, smem attributes
-// inverse: nf spectral value fields (in[f]) -> physical (out[f])
+// inverse: nf spectral value fields (in[f]) -> physical (out[f]); in the precision path (precision 1) the
+// inputs are the double-float pairs the evaluation kernels store
 void fft_inverse(Ctx& c, cd* const* in, double* const* out, int nf);
 // forward: nf physical fields -> spectral value fields, truncated and scaled
 void fft_forward(Ctx& c, double* const* in, cd* const* out, int nf);
@@ -331,7 +332,7 @@ void fft_forward_as(Ctx& c, double* const* in, cd* const* out, int nf, int preci
 // the fixed point's products formed inside the x-passes (Sec. 4.3): inverse transform of one field whose
 // x-pass stores w * phys (rho_t = f'(z) dz/dt), and forward transform of -(w1 m1 + w2 m2 + w3 m3) formed
 // in the x-pass prologue (the tail of L); w, m: physical fields in the arithmetic of the precision
-void fft_inverse_mul(Ctx& c, cd* in, double* out, const double* w);
+void fft_inverse_mul(Ctx& c, cd* in, double* out, const double* w);  // input as for fft_inverse
 void fft_forward_dot3(Ctx& c, const double* const* w, const double* const* m, cd* out);
 
 }  // namespace lmvd

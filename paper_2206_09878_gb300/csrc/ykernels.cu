@@ -104,6 +104,14 @@ __device__ __forceinline__ cdf cd_to_cdf(cd x) { return cdf{df_from_double_int(x
 __device__ __forceinline__ cd cdf_to_cd(cdf x) {
   return cd{df_to_double_int(drenorm(x.re)), df_to_double_int(drenorm(x.im))};
 }
+// The values these evaluations produce feed only the precision path's inverse transforms, whose z-pass
+// works in double-float: they are stored as renormalised pairs (cdf, the same 16 bytes as a complex
+// double) and the z-pass reads them as they are (fft_inverse_df_in), so neither side converts.
+__device__ __forceinline__ void put_df(cd* p, size_t o, cdf v) {
+  reinterpret_cast<cdf*>(p)[o] = cdf{drenorm(v.re), drenorm(v.im)};
+}
+__device__ __forceinline__ void put_df(cd* p, size_t o, cd v) { reinterpret_cast<cdf*>(p)[o] = cd_to_cdf(v); }
+
 // A thread walks the rows of one mode, and a band's first column c0[i] never decreases and grows by at
 // most one per row (Greville points are at most one knot interval apart), so each input coefficient is
 // split into a double-float pair once and kept in a register window of the W columns c .. c + W - 1
@@ -176,20 +184,20 @@ __global__ void __launch_bounds__(128) k_eval_p1_df(Grid g, DBand B0g, DBand B1g
   row_range(g.ny, blockIdx.y, gridDim.y, r0, r1);
   if (is_nyquist(g, m)) {
     for (int i = r0; i < r1; ++i)
-      for (int f = 0; f < 8; ++f) out.p[f][(size_t)i * M + m] = mk(0, 0);
+      for (int f = 0; f < 8; ++f) put_df(out.p[f], (size_t)i * M + m, mk(0, 0));
     return;
   }
   if (m == 0) {  // the plane means and the k = 0 z values: one mode, kept in FP64
     for (int i = r0; i < r1; ++i) {
       const size_t o = (size_t)i * M;
-      out.p[0][o] = band_row(B0g, i, z, M, 0);
-      out.p[1][o] = mk(0, 0);
-      out.p[2][o] = mk(0, 0);
-      out.p[3][o] = band_row(B1g, i, z, M, 0);
-      out.p[4][o] = band_row(B2g, i, z, M, 0);
-      out.p[5][o] = mk(band_row_real(B0g, i, mm1), 0.0);
-      out.p[6][o] = mk(0, 0);
-      out.p[7][o] = mk(band_row_real(B0g, i, mm3), 0.0);
+      put_df(out.p[0], o, band_row(B0g, i, z, M, 0));
+      put_df(out.p[1], o, mk(0, 0));
+      put_df(out.p[2], o, mk(0, 0));
+      put_df(out.p[3], o, band_row(B1g, i, z, M, 0));
+      put_df(out.p[4], o, band_row(B2g, i, z, M, 0));
+      put_df(out.p[5], o, mk(band_row_real(B0g, i, mm1), 0.0));
+      put_df(out.p[6], o, mk(0, 0));
+      put_df(out.p[7], o, mk(band_row_real(B0g, i, mm3), 0.0));
     }
     return;
   }
@@ -217,22 +225,23 @@ __global__ void __launch_bounds__(128) k_eval_p1_df(Grid g, DBand B0g, DBand B1g
     const cdf zg = wz.dot(B0g, i), zy = wz.dot(B1g, i), zyy = wz.dot(B2g, i);
     const cdf dm2 = wm.dot(Sg1, i), omg = wo.dot(B0g, i);
     const cdf zgr{drenorm(zg.re), drenorm(zg.im)};
-    out.p[0][o] = cdf_to_cd(zgr);
-    out.p[1][o] = cdf_to_cd(cdf{dmul(nk1, zgr.im), dmul(k1, zgr.re)});   // i k1 z
-    out.p[2][o] = cdf_to_cd(cdf{dmul(nk3, zgr.im), dmul(k3, zgr.re)});   // i k3 z
-    out.p[3][o] = cdf_to_cd(zy);
-    out.p[4][o] = cdf_to_cd(cdf_add_lazy(cdf{dmul(nk2, zgr.re), dmul(nk2, zgr.im)}, zyy));  // -k^2 z + z''
+    put_df(out.p[0], o, zgr);
+    put_df(out.p[1], o, cdf{dmul(nk1, zgr.im), dmul(k1, zgr.re)});   // i k1 z
+    put_df(out.p[2], o, cdf{dmul(nk3, zgr.im), dmul(k3, zgr.re)});   // i k3 z
+    put_df(out.p[3], o, zy);
+    put_df(out.p[4], o, cdf_add_lazy(cdf{dmul(nk2, zgr.re), dmul(nk2, zgr.im)}, zyy));  // -k^2 z + z''
     const cdf dmr{drenorm(dm2.re), drenorm(dm2.im)}, omr{drenorm(omg.re), drenorm(omg.im)};
     // m1^d = (i k1 dm2 - i k3 om) / k^2, m3^d = (i k3 dm2 + i k1 om) / k^2 (Eq. md_recon)
     const df a1 = ddot2(k1, dmr.re, nk3, omr.re), b1 = ddot2(k1, dmr.im, nk3, omr.im);
     const df a3 = ddot2(k3, dmr.re, k1, omr.re), b3 = ddot2(k3, dmr.im, k1, omr.im);
-    out.p[5][o] = cdf_to_cd(cdf{dmul(ik2, dneg(b1)), dmul(ik2, a1)});
-    out.p[6][o] = cdf_to_cd(wm.dot(Sg0, i));
-    out.p[7][o] = cdf_to_cd(cdf{dmul(ik2, dneg(b3)), dmul(ik2, a3)});
+    put_df(out.p[5], o, cdf{dmul(ik2, dneg(b1)), dmul(ik2, a1)});
+    put_df(out.p[6], o, wm.dot(Sg0, i));
+    put_df(out.p[7], o, cdf{dmul(ik2, dneg(b3)), dmul(ik2, a3)});
   }
 }
 
-// k_eval in double-float (jobs without accumulation into out); W: the widest band of the jobs
+// k_eval in double-float (jobs without accumulation into out; values as double-float pairs); W: the widest
+// band of the jobs
 template <int W>
 __global__ void __launch_bounds__(128) k_eval_df(Grid g, EvalJobs jobs) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
@@ -245,12 +254,12 @@ __global__ void __launch_bounds__(128) k_eval_df(Grid g, EvalJobs jobs) {
   DfWin<W> win;
   for (int i = r0; i < r1; ++i) {
     if (ny) {
-      jb.out[(size_t)i * M + m] = mk(0, 0);
+      put_df(jb.out, (size_t)i * M + m, mk(0, 0));
       continue;
     }
     win.seek(jb.in, M, m, __ldg(jb.B.c0 + i), jb.B.cols);
     if (i + 1 < r1) win.prefetch(jb.in, M, m, __ldg(jb.B.c0 + i + 1), jb.B.cols);
-    jb.out[(size_t)i * M + m] = cdf_to_cd(win.dot(jb.B, i));
+    put_df(jb.out, (size_t)i * M + m, win.dot(jb.B, i));
   }
 }
 

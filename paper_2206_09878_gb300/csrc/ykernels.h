@@ -63,7 +63,8 @@ __global__ void k_eval_p1(Grid g, DBand B0g, DBand B1g, DBand B2g, DBand Sg0, DB
                           const cd* om, const cd* m2, const double* mm1, const double* mm3, Fields8 out);
 __global__ void k_eval(Grid g, EvalJobs jobs);
 // double-float evaluations of the precision path (same outputs as k_eval_p1, k_eval without accumulation and
-// k_rhs_eval), launched on st for spline orders p = 4..8 (band widths w = 4..9)
+// k_rhs_eval), launched on st for spline orders p = 4..8 (band widths w = 4..9). The first two store their
+// values as double-float pairs (for fft_inverse_df_in), the third FP64 values (for the FP64 RK update).
 void launch_eval_p1_df(int p, dim3 grid, int tpb, cudaStream_t st, const Grid& g, const DBand& B0g, const DBand& B1g,
                        const DBand& B2g, const DBand& Sg0, const DBand& Sg1, const cd* z, const cd* om, const cd* m2,
                        const double* mm1, const double* mm3, const Fields8& out);
