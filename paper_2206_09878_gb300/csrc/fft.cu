@@ -198,6 +198,9 @@ __device__ void fft_inplace(C* x, const FFTPlan& pl, int tt, int tpt) {
 // (separated by barriers) overlap: 7-8% faster in double-float at 512^3. The z-passes gather `batch` kx
 // columns of each z-row, so they keep 4 of them per CTA (64-byte row segments; 3 CTAs per SM).
 constexpr int FFT_CTA_X = 128, FFT_MIN_CTAS_X = 6, FFT_CTA_Z = 256, FFT_MIN_CTAS_Z = 3;
+// Loads a thread issues in its gather / scatter loops before it stores any of them: one load at a time would
+// serialise a memory latency per iteration (ncu: long-scoreboard stalls dominated the double-float passes).
+constexpr int FFT_LOAD_CHUNK = 4;
 
 // ---------------------------------------------------------------- inverse z-pass
 // in: spectral value fields [ny][nz][nxh] (complex double); T: [f][ny][pz][nx/2] of C
@@ -214,15 +217,27 @@ __global__ void __launch_bounds__(FFT_CTA_Z, FFT_MIN_CTAS_Z) k_fft_z_inv(FFTPlan
   for (int idx = threadIdx.x; idx < batch * ld; idx += blockDim.x) a[idx] = F::zero();
   __syncthreads();
   const cd* src = pick(in.p, f) + (size_t)j * g.M;
-  for (int idx = threadIdx.x; idx < nz * batch; idx += blockDim.x) {
-    const int jz = idx / batch, bb = idx - jz * batch, kx = kx0 + bb;
-    if (kx < h && jz != nz / 2) {
-      const int pos = jz < nz / 2 ? jz : pz - nz + jz;
-      if (LMVD_IN(bb * ld + pos, batch * ld) && LMVD_IN((size_t)jz * g.nxh + kx, g.M)) {
-        if constexpr (IN_DF) a[bb * ld + pos] = reinterpret_cast<const C*>(src)[(size_t)jz * g.nxh + kx];
-        else a[bb * ld + pos] = F::from_spec(src[(size_t)jz * g.nxh + kx]);
+  for (int base = threadIdx.x; base < nz * batch; base += FFT_LOAD_CHUNK * blockDim.x) {
+    C v[FFT_LOAD_CHUNK];
+    int d[FFT_LOAD_CHUNK];
+#pragma unroll
+    for (int u = 0; u < FFT_LOAD_CHUNK; ++u) {
+      const int idx = base + u * blockDim.x;
+      d[u] = -1;
+      if (idx >= nz * batch) continue;
+      const int jz = idx / batch, bb = idx - jz * batch, kx = kx0 + bb;
+      if (kx < h && jz != nz / 2) {
+        const int pos = jz < nz / 2 ? jz : pz - nz + jz;
+        if (LMVD_IN(bb * ld + pos, batch * ld) && LMVD_IN((size_t)jz * g.nxh + kx, g.M)) {
+          d[u] = bb * ld + pos;
+          if constexpr (IN_DF) v[u] = reinterpret_cast<const C*>(src)[(size_t)jz * g.nxh + kx];
+          else v[u] = F::from_spec(src[(size_t)jz * g.nxh + kx]);
+        }
       }
     }
+#pragma unroll
+    for (int u = 0; u < FFT_LOAD_CHUNK; ++u)
+      if (d[u] >= 0) a[d[u]] = v[u];
   }
   __syncthreads();
   fft_inplace<C, 1, EPT>(a + bt * ld, pl, tt, pl.tpt);
@@ -252,39 +267,78 @@ __device__ __forceinline__ void x_inv_body(const FFTPlan& pl, const Grid& g, con
   for (int idx = threadIdx.x; idx < batch * ld; idx += blockDim.x) a[idx] = F::zero();
   __syncthreads();
   const C* src = T + f * tstride + (size_t)j * pz * h;
-  for (int idx = threadIdx.x; idx < batch * h; idx += blockDim.x) {
-    const int bb = idx / h, k = idx - bb * h;
-    const int za = 2 * (pr0 + bb), zb = za + 1;
-    if (za >= pz) continue;
-    if (!LMVD_IN((size_t)za * h + k, (size_t)pz * h) || !LMVD_IN(bb * ld + px - 1, batch * ld)) continue;
-    const C ta = src[(size_t)za * h + k];
-    const C tb = zb < pz ? src[(size_t)zb * h + k] : F::zero();
-    C* y = a + bb * ld;
-    if (k == 0) {
-      y[0] = F::make(F::re(ta), F::re(tb));  // the kx = 0 coefficient of a real row is real
-    } else {
-      y[k] = F::add(ta, F::ti(tb));                     // Xa[k] + i Xb[k]
-      y[px - k] = F::add(F::cj(ta), F::ti(F::cj(tb)));  // conj(Xa[k]) + i conj(Xb[k])
+  for (int base = threadIdx.x; base < batch * h; base += FFT_LOAD_CHUNK * blockDim.x) {
+    C ta[FFT_LOAD_CHUNK], tb[FFT_LOAD_CHUNK];
+    int kk[FFT_LOAD_CHUNK], bs[FFT_LOAD_CHUNK];
+#pragma unroll
+    for (int u = 0; u < FFT_LOAD_CHUNK; ++u) {
+      const int idx = base + u * blockDim.x;
+      kk[u] = -1;
+      if (idx >= batch * h) continue;
+      const int bb = idx / h, k = idx - bb * h;
+      const int za = 2 * (pr0 + bb), zb = za + 1;
+      if (za >= pz) continue;
+      if (!LMVD_IN((size_t)za * h + k, (size_t)pz * h) || !LMVD_IN(bb * ld + px - 1, batch * ld)) continue;
+      kk[u] = k;
+      bs[u] = bb;
+      ta[u] = src[(size_t)za * h + k];
+      tb[u] = zb < pz ? src[(size_t)zb * h + k] : F::zero();
+    }
+#pragma unroll
+    for (int u = 0; u < FFT_LOAD_CHUNK; ++u) {
+      if (kk[u] < 0) continue;
+      const int k = kk[u];
+      C* y = a + bs[u] * ld;
+      if (k == 0) {
+        y[0] = F::make(F::re(ta[u]), F::re(tb[u]));  // the kx = 0 coefficient of a real row is real
+      } else {
+        y[k] = F::add(ta[u], F::ti(tb[u]));                        // Xa[k] + i Xb[k]
+        y[px - k] = F::add(F::cj(ta[u]), F::ti(F::cj(tb[u])));  // conj(Xa[k]) + i conj(Xb[k])
+      }
     }
   }
   __syncthreads();
   fft_inplace<C, 1, EPT>(a + bt * ld, pl, tt, pl.tpt);
   const C* res = a;
   R* dst = reinterpret_cast<R*>(pick(out.p, f)) + (size_t)j * g.P;
+  if (MUL) {
+    const R* w = reinterpret_cast<const R*>(wmul) + (size_t)j * g.P;
+    for (int base = threadIdx.x; base < batch * px; base += FFT_LOAD_CHUNK * blockDim.x) {
+      R wa[FFT_LOAD_CHUNK], wb[FFT_LOAD_CHUNK];
+      int xs[FFT_LOAD_CHUNK], bs[FFT_LOAD_CHUNK];
+#pragma unroll
+      for (int u = 0; u < FFT_LOAD_CHUNK; ++u) {
+        const int idx = base + u * blockDim.x;
+        xs[u] = -1;
+        if (idx >= batch * px) continue;
+        const int bb = idx / px, x = idx - bb * px;
+        const int za = 2 * (pr0 + bb), zb = za + 1;
+        if (za >= pz) continue;
+        if (!LMVD_IN((size_t)za * px + x, g.P) || !LMVD_IN(bb * ld + x, batch * ld)) continue;
+        xs[u] = x;
+        bs[u] = bb;
+        wa[u] = w[(size_t)za * px + x];
+        wb[u] = zb < pz ? w[(size_t)zb * px + x] : F::rzero();
+      }
+#pragma unroll
+      for (int u = 0; u < FFT_LOAD_CHUNK; ++u) {
+        if (xs[u] < 0) continue;
+        const int x = xs[u], za = 2 * (pr0 + bs[u]), zb = za + 1;
+        const C v = res[bs[u] * ld + x];
+        dst[(size_t)za * px + x] = F::rmul(wa[u], F::re(v));
+        if (zb < pz) dst[(size_t)zb * px + x] = F::rmul(wb[u], F::im(v));
+      }
+    }
+    return;
+  }
   for (int idx = threadIdx.x; idx < batch * px; idx += blockDim.x) {
     const int bb = idx / px, x = idx - bb * px;
     const int za = 2 * (pr0 + bb), zb = za + 1;
     if (za >= pz) continue;
     if (!LMVD_IN((size_t)za * px + x, g.P) || !LMVD_IN(bb * ld + x, batch * ld)) continue;
     const C v = res[bb * ld + x];
-    if (MUL) {
-      const R* w = reinterpret_cast<const R*>(wmul) + (size_t)j * g.P;
-      dst[(size_t)za * px + x] = F::rmul(w[(size_t)za * px + x], F::re(v));
-      if (zb < pz) dst[(size_t)zb * px + x] = F::rmul(w[(size_t)zb * px + x], F::im(v));
-    } else {
-      dst[(size_t)za * px + x] = F::re(v);
-      if (zb < pz) dst[(size_t)zb * px + x] = F::im(v);
-    }
+    dst[(size_t)za * px + x] = F::re(v);
+    if (zb < pz) dst[(size_t)zb * px + x] = F::im(v);
   }
 }
 template <class C, int EPT>
@@ -316,31 +370,45 @@ __device__ __forceinline__ void x_fwd_body(const FFTPlan& pl, const Grid& g, con
   const int pr0 = blockIdx.x * batch, j = blockIdx.y, f = blockIdx.z;
   const int bt = threadIdx.x / pl.tpt, tt = threadIdx.x - bt * pl.tpt;
   const R* src = reinterpret_cast<const R*>(pick(in.p, f)) + (size_t)j * g.P;
-  for (int idx = threadIdx.x; idx < batch * px; idx += blockDim.x) {
-    const int bb = idx / px, x = idx - bb * px;
-    const int za = 2 * (pr0 + bb), zb = za + 1;
-    R va = F::rzero(), vb = F::rzero();
-    if (za < pz && LMVD_IN((size_t)za * px + x, g.P)) {
-      if (DOT3) {
-        const size_t plane = (size_t)j * g.P;
-        const R* w0 = reinterpret_cast<const R*>(d.w[0]) + plane;
-        const R* w1 = reinterpret_cast<const R*>(d.w[1]) + plane;
-        const R* w2 = reinterpret_cast<const R*>(d.w[2]) + plane;
-        const R* m0 = reinterpret_cast<const R*>(d.m[0]) + plane;
-        const R* m1 = reinterpret_cast<const R*>(d.m[1]) + plane;
-        const R* m2 = reinterpret_cast<const R*>(d.m[2]) + plane;
-        size_t o = (size_t)za * px + x;
-        va = F::dot3neg(w0[o], m0[o], w1[o], m1[o], w2[o], m2[o]);
-        if (zb < pz) {
-          o += px;
-          vb = F::dot3neg(w0[o], m0[o], w1[o], m1[o], w2[o], m2[o]);
+  // DOT3 reads six fields per point: fewer points per chunk keep the registers in check
+  constexpr int CH = DOT3 ? 2 : FFT_LOAD_CHUNK;
+  for (int base = threadIdx.x; base < batch * px; base += CH * blockDim.x) {
+    R va[CH], vb[CH];
+    int ds[CH];
+#pragma unroll
+    for (int u = 0; u < CH; ++u) {
+      const int idx = base + u * blockDim.x;
+      ds[u] = -1;
+      va[u] = vb[u] = F::rzero();
+      if (idx >= batch * px) continue;
+      const int bb = idx / px, x = idx - bb * px;
+      const int za = 2 * (pr0 + bb), zb = za + 1;
+      if (!LMVD_IN(bb * ld + x, batch * ld)) continue;
+      ds[u] = bb * ld + x;
+      if (za < pz && LMVD_IN((size_t)za * px + x, g.P)) {
+        if (DOT3) {
+          const size_t plane = (size_t)j * g.P;
+          const R* w0 = reinterpret_cast<const R*>(d.w[0]) + plane;
+          const R* w1 = reinterpret_cast<const R*>(d.w[1]) + plane;
+          const R* w2 = reinterpret_cast<const R*>(d.w[2]) + plane;
+          const R* m0 = reinterpret_cast<const R*>(d.m[0]) + plane;
+          const R* m1 = reinterpret_cast<const R*>(d.m[1]) + plane;
+          const R* m2 = reinterpret_cast<const R*>(d.m[2]) + plane;
+          size_t o = (size_t)za * px + x;
+          va[u] = F::dot3neg(w0[o], m0[o], w1[o], m1[o], w2[o], m2[o]);
+          if (zb < pz) {
+            o += px;
+            vb[u] = F::dot3neg(w0[o], m0[o], w1[o], m1[o], w2[o], m2[o]);
+          }
+        } else {
+          va[u] = src[(size_t)za * px + x];
+          if (zb < pz) vb[u] = src[(size_t)zb * px + x];
         }
-      } else {
-        va = src[(size_t)za * px + x];
-        if (zb < pz) vb = src[(size_t)zb * px + x];
       }
     }
-    if (LMVD_IN(bb * ld + x, batch * ld)) a[bb * ld + x] = F::make(va, vb);
+#pragma unroll
+    for (int u = 0; u < CH; ++u)
+      if (ds[u] >= 0) a[ds[u]] = F::make(va[u], vb[u]);
   }
   __syncthreads();
   fft_inplace<C, -1, EPT>(a + bt * ld, pl, tt, pl.tpt);
@@ -376,10 +444,22 @@ __global__ void __launch_bounds__(FFT_CTA_Z, FFT_MIN_CTAS_Z) k_fft_z_fwd(FFTPlan
   const int kx0 = blockIdx.x * batch, j = blockIdx.y, f = blockIdx.z;
   const int bt = threadIdx.x / pl.tpt, tt = threadIdx.x - bt * pl.tpt;
   const C* src = T + f * tstride + (size_t)j * pz * h;
-  for (int idx = threadIdx.x; idx < pz * batch; idx += blockDim.x) {
-    const int zz = idx / batch, bb = idx - zz * batch, kx = kx0 + bb;
-    if (LMVD_IN(bb * ld + zz, batch * ld))
-      a[bb * ld + zz] = (kx < h && LMVD_IN((size_t)zz * h + kx, (size_t)pz * h)) ? src[(size_t)zz * h + kx] : F::zero();
+  for (int base = threadIdx.x; base < pz * batch; base += FFT_LOAD_CHUNK * blockDim.x) {
+    C v[FFT_LOAD_CHUNK];
+    int d[FFT_LOAD_CHUNK];
+#pragma unroll
+    for (int u = 0; u < FFT_LOAD_CHUNK; ++u) {
+      const int idx = base + u * blockDim.x;
+      d[u] = -1;
+      if (idx >= pz * batch) continue;
+      const int zz = idx / batch, bb = idx - zz * batch, kx = kx0 + bb;
+      if (!LMVD_IN(bb * ld + zz, batch * ld)) continue;
+      d[u] = bb * ld + zz;
+      v[u] = (kx < h && LMVD_IN((size_t)zz * h + kx, (size_t)pz * h)) ? src[(size_t)zz * h + kx] : F::zero();
+    }
+#pragma unroll
+    for (int u = 0; u < FFT_LOAD_CHUNK; ++u)
+      if (d[u] >= 0) a[d[u]] = v[u];
   }
   __syncthreads();
   fft_inplace<C, -1, EPT>(a + bt * ld, pl, tt, pl.tpt);
