@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(FFT_CTA_Z, FFT_MIN_CTAS_Z) k_fft_z_inv(FFTPlan
   using F = FT<C>;
   extern __shared__ __align__(16) unsigned char sm_raw[];
   C* a = reinterpret_cast<C*>(sm_raw);
-  const int batch = pl.batch, ld = pl.n + 1, pz = g.pz, nz = g.nz, h = g.nx / 2;
+  const int batch = pl.batch, ld = pl.n + pl.pad, pz = g.pz, nz = g.nz, h = g.nx / 2;
   const int kx0 = blockIdx.x * batch, j = blockIdx.y, f = blockIdx.z;
   const int bt = threadIdx.x / pl.tpt, tt = threadIdx.x - bt * pl.tpt;
   for (int idx = threadIdx.x; idx < batch * ld; idx += blockDim.x) a[idx] = F::zero();
@@ -261,7 +261,7 @@ __device__ __forceinline__ void x_inv_body(const FFTPlan& pl, const Grid& g, con
   using R = typename F::R;
   extern __shared__ __align__(16) unsigned char sm_raw[];
   C* a = reinterpret_cast<C*>(sm_raw);
-  const int batch = pl.batch, ld = pl.n + 1, px = g.px, pz = g.pz, h = g.nx / 2;
+  const int batch = pl.batch, ld = pl.n + pl.pad, px = g.px, pz = g.pz, h = g.nx / 2;
   const int pr0 = blockIdx.x * batch, j = blockIdx.y, f = blockIdx.z;
   const int bt = threadIdx.x / pl.tpt, tt = threadIdx.x - bt * pl.tpt;
   for (int idx = threadIdx.x; idx < batch * ld; idx += blockDim.x) a[idx] = F::zero();
@@ -366,7 +366,7 @@ __device__ __forceinline__ void x_fwd_body(const FFTPlan& pl, const Grid& g, con
   using R = typename F::R;
   extern __shared__ __align__(16) unsigned char sm_raw[];
   C* a = reinterpret_cast<C*>(sm_raw);
-  const int batch = pl.batch, ld = pl.n + 1, px = g.px, pz = g.pz, h = g.nx / 2;
+  const int batch = pl.batch, ld = pl.n + pl.pad, px = g.px, pz = g.pz, h = g.nx / 2;
   const int pr0 = blockIdx.x * batch, j = blockIdx.y, f = blockIdx.z;
   const int bt = threadIdx.x / pl.tpt, tt = threadIdx.x - bt * pl.tpt;
   const R* src = reinterpret_cast<const R*>(pick(in.p, f)) + (size_t)j * g.P;
@@ -440,7 +440,7 @@ __global__ void __launch_bounds__(FFT_CTA_Z, FFT_MIN_CTAS_Z) k_fft_z_fwd(FFTPlan
   using F = FT<C>;
   extern __shared__ __align__(16) unsigned char sm_raw[];
   C* a = reinterpret_cast<C*>(sm_raw);
-  const int batch = pl.batch, ld = pl.n + 1, pz = g.pz, nz = g.nz, h = g.nx / 2;
+  const int batch = pl.batch, ld = pl.n + pl.pad, pz = g.pz, nz = g.nz, h = g.nx / 2;
   const int kx0 = blockIdx.x * batch, j = blockIdx.y, f = blockIdx.z;
   const int bt = threadIdx.x / pl.tpt, tt = threadIdx.x - bt * pl.tpt;
   const C* src = T + f * tstride + (size_t)j * pz * h;
@@ -478,7 +478,7 @@ __global__ void __launch_bounds__(FFT_CTA_Z, FFT_MIN_CTAS_Z) k_fft_z_fwd(FFTPlan
 // ---------------------------------------------------------------- host side
 // Radix order 4s, 2s, 3s: the sub-length L is a power of two in every radix-4/2 stage (mask arithmetic).
 // 12 elements per thread (6 when n has a single factor 2, hence no radix-4 stage); at most cta threads per
-// CTA (so n <= 12 cta); one shared buffer of batch transforms with leading dimension n + 1.
+// CTA (so n <= 12 cta); one shared buffer of batch transforms with leading dimension n + pad.
 static bool make_plan(int n, int cta, FFTPlan& p) {
   p.n = n;
   p.nst = 0;
@@ -495,10 +495,15 @@ static bool make_plan(int n, int cta, FFTPlan& p) {
   p.tpt = n / p.ept;
   if (p.tpt > cta) return false;
   p.batch = cta / p.tpt;
+  // leading dimension n + pad of a transform in shared memory. The z-passes gather and scatter their batch of
+  // columns with the column index fastest across threads: with n + 2 the 16-byte elements of four columns at
+  // the same position land in distinct bank groups (n + 1 put neighbouring positions of adjacent columns in
+  // the same one: 2-way conflicts). The x-passes walk one transform contiguously and keep n + 1.
+  p.pad = cta == FFT_CTA_Z ? 2 : 1;
   return true;
 }
 
-static size_t smem_bytes(const FFTPlan& p) { return (size_t)p.batch * (p.n + 1) * sizeof(cd); }
+static size_t smem_bytes(const FFTPlan& p) { return (size_t)p.batch * (p.n + p.pad) * sizeof(cd); }
 static unsigned threads(const FFTPlan& p) { return (unsigned)(p.batch * p.tpt); }
 
 static df host_split(long double x) {
