@@ -38,13 +38,14 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # df64.h (TwoSum-renormalised adds, FMA TwoProd products), i.e. 10 instructions per classic flop;
 # the FP32 pipe issues 152 SMs x 128 lanes x 2.07 GHz instructions per second.
 DF64_EQ_PEAK_TFLOPS = 152 * 128 * 2.07e9 / 10 / 1e12
-# DRAM bytes (read + write) per unit of the dominant kernel from one ncu capture of a smaller case with the
-# same transform length, keyed by (precision, kernel class, transform length); a unit of the x-passes is one
-# complex transform (a pair of real rows). Full launches are scaled by the units they process.
-#   (0, fft_x_inverse, 768): 2025.8 MB over 101376 units (512 x 33 x 512, 8 fields) = 19983 B per unit,
-#   (1, fft_x_inverse, 768): 2031.4 MB over the same units = 20038 B per unit,
-#   against 2 (16 nx/2 + 8 px) = 20480 algorithmic bytes.
-NCU_DRAM_BYTES_PER_UNIT = {(0, "fft_x_inverse", 768): 18550.0, (1, "fft_x_inverse", 768): 18422.0}
+# Measured DRAM bytes (read + write) of the dominant kernel class over its algorithmic bytes, from one ncu
+# capture of a smaller case with the same transform length (512 x 33 x 512: 768-point x-transforms), keyed by
+# (precision, kernel class, transform length). The class fft_x_inverse holds k_fft_x_inv (19094 / 18996 B per
+# complex x-transform against 20480 algorithmic) and k_fft_x_inv_mul, whose epilogue also reads f' (29829 /
+# 29622 B against 32768); over the 12 launches of one substage the measured bytes are these fractions of the
+# algorithmic ones (profiles/fft_x_inverse_rt512y33_traffic.md). Full launches: the fraction times the
+# launch's algorithmic bytes.
+NCU_DRAM_FRACTION = {(0, "fft_x_inverse", 768): 0.9266, (1, "fft_x_inverse", 768): 0.9215}
 CPU_SAMPLE_N = 128
 
 
@@ -284,21 +285,21 @@ def time_variant(L, w, precision, args, stream, st_host, local, ws, e2e_steps=0)
 
 
 def traffic_per_launch(fp, kernel, grid, alg_bytes_per_launch):
-    """DRAM bytes per launch from the ncu per-unit figure (None where no capture matches)."""
+    """DRAM bytes per launch from the ncu fraction of the algorithmic bytes (None where no capture matches)."""
     nx, _, nz = grid
     px = 3 * nx // 2
-    per_unit = NCU_DRAM_BYTES_PER_UNIT.get((fp, kernel, px))
-    if per_unit is None or not kernel.startswith("fft_x") or not alg_bytes_per_launch:
+    frac = NCU_DRAM_FRACTION.get((fp, kernel, px))
+    if frac is None or not alg_bytes_per_launch:
         return None
-    units = alg_bytes_per_launch / (2.0 * (16 * (nx // 2) + 8 * px))
-    return per_unit * units
+    return frac * alg_bytes_per_launch
 
 
 def measured_rates(L, iters=4000):
     """Issue rates of this GPU from the library's probe (lmvd_rate_probe): FP64 FMA / add / multiply and
-    FP32 FMA, operations per second (8 independent chains per thread, 8 CTAs of 256 per SM)."""
+    FP32 FMA, operations per second (8 independent chains per thread, 8 CTAs of 256 per SM). The FP32 probe
+    runs 50x the iterations, so that it too lasts ~10 ms and the launch costs < 0.1% of its time."""
     names = ("fp64_fma", "fp64_add", "fp64_mul", "fp32_fma")
-    return {n: L.lmvd_rate_probe(op, iters) for op, n in enumerate(names)}
+    return {n: L.lmvd_rate_probe(op, iters * (50 if n == "fp32_fma" else 1)) for op, n in enumerate(names)}
 
 
 def roofline_of(prof, ms_step_total, fp, grid, rates=None):
@@ -321,8 +322,9 @@ def roofline_of(prof, ms_step_total, fp, grid, rates=None):
     return {"kernel": top, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak if achieved else None,
             "traffic": traffic_per_launch(fp, top, grid, tby / tn if tn else None),
-            "traffic_note": "ncu dram__bytes_read.sum + dram__bytes_write.sum per unit on 512x33x512 (same "
-                            "768-point transforms), scaled by the units of the average launch",
+            "traffic_note": "ncu dram__bytes_read.sum + dram__bytes_write.sum over the algorithmic bytes of the "
+                            "class on 512x33x512 (same 768-point transforms), times the average launch's "
+                            "algorithmic bytes",
             "launches": int(tn), "algorithmic_bytes_per_launch": tby / tn if tn else None,
             "achieved_hbm_gbs": tby / (tms / 1e3) / 1e9 if tms > 0 else None, "peak_note": note,
             "share_of_step": tms / ms_step_total if ms_step_total > 0 else None}

@@ -1,7 +1,7 @@
 """CPU checks of the arithmetic behind bench.py's `roofline` object: the dominant class is the one with the
 most kernel time, achieved = its algorithmic flops / its summed kernel time, frac = achieved / peak of its
-arithmetic, and the DRAM traffic is the ncu bytes per unit (one complex px-point x-transform) times the
-units of the class's average launch, whose algorithmic bytes are 2 (16 nx/2 + 8 px) per unit."""
+arithmetic, and the DRAM traffic is the ncu fraction of the class's algorithmic bytes times the algorithmic
+bytes of its average launch."""
 import pytest
 
 
@@ -18,11 +18,10 @@ def test_dominant_class_and_rates():
     assert r["launches"] == 10 and r["algorithmic_bytes_per_launch"] == pytest.approx(9.0e9)
     assert r["achieved_hbm_gbs"] == pytest.approx(9.0e10 / 0.2 / 1e9)
     assert r["share_of_step"] == pytest.approx(0.5)
-    units = 9.0e9 / (2.0 * (16 * 256 + 8 * 768))
-    assert r["traffic"] == pytest.approx(bench.NCU_DRAM_BYTES_PER_UNIT[(0, "fft_x_inverse", 768)] * units)
+    assert r["traffic"] == pytest.approx(bench.NCU_DRAM_FRACTION[(0, "fft_x_inverse", 768)] * 9.0e9)
     rd = bench.roofline_of(prof, 400.0, 1, (512, 513, 512))
     assert rd["peak"] == pytest.approx(152 * 128 * 2.07e9 / 10 / 1e12)
-    assert rd["traffic"] == pytest.approx(bench.NCU_DRAM_BYTES_PER_UNIT[(1, "fft_x_inverse", 768)] * units)
+    assert rd["traffic"] == pytest.approx(bench.NCU_DRAM_FRACTION[(1, "fft_x_inverse", 768)] * 9.0e9)
 
 
 def test_traffic_is_null_without_a_matching_capture():
