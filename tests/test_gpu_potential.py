@@ -11,7 +11,8 @@ of H is ~3e-6 of H), and the mean-momentum RHS vanishes by the reflection symmet
 Omega2 is compared against the oracle's own conditioning: the change of the oracle's Omega2 when its
 z input moves by one FP64 rounding unit 2^-52 (measured in the test, ~3e-11 relative), scaled to the
 unit roundoff of the arithmetic that formed the products (2^-48 for double-float). The whole horizontal
-momentum components m1, m3, which contain Omega2, keep the 1e-12 bar.
+momentum components m1, m3, which contain Omega2, keep the 1e-12 bar. Every intermediate of each
+substage (dz/dt, R_z, rho_t, m^c, the right-hand sides) is held to the same bounds as in the wall cases.
 """
 import numpy as np
 import pytest
@@ -50,12 +51,13 @@ def _boundary_rows(S, gpu, mc2):
     return out
 
 
-def _run(L, S, ctx, st, nsub):
-    from _pairs import compare_states, to_numpy, to_torch
-    from test_gpu_parity import _field_errors
+def _run(L, S, ctx, st, nsub, cfg, precision):
+    """nsub substages of both sides; the worst state errors, the worst boundary-row residuals, and every
+    intermediate (dz/dt, R_z, rho_t, m^c, right-hand sides) outside its bound, as in the wall cases."""
+    from _pairs import compare_states, gpu_intermediates, intermediate_check, oracle_intermediates, to_numpy, to_torch
     S.set_state(**st)
     ctx.set_state(to_torch(st))
-    worst, rows = {}, {}
+    worst, rows, over_tol = {}, {}, []
     for s in range(nsub):
         S.advance_substage()
         ctx.advance_substage()
@@ -63,23 +65,25 @@ def _run(L, S, ctx, st, nsub):
         mc2 = ctx.field(L.LMVD_FIELD_MC2).cpu().numpy()
         ctx.synchronize()
         e = compare_states(S, gpu, S.state())
-        fe = _field_errors(L, S, ctx)
+        fe, tol = intermediate_check(S, cfg, gpu_intermediates(L, ctx), oracle_intermediates(S), precision)
         print("substage", s, {k: "%.1e" % v for k, v in {**e, **fe}.items()})
         for k, v in e.items():
             worst[k] = max(worst.get(k, 0.0), v)
         for k, v in _boundary_rows(S, gpu, mc2).items():
             rows[k] = max(rows.get(k, 0.0), v)
-    return worst, rows
+        over_tol += [(s, k, v, tol[k]) for k, v in fe.items() if not v <= tol[k]]
+    return worst, rows, over_tol
 
 
 @pytest.mark.parametrize("precision", [0, 1])
 def test_random_momentum_potential_matches_oracle(L, precision):
     from _pairs import make_pair
     S, ctx, st, cfg = make_pair(L, "rt32", precision=precision, u_rms=1e-2, bc="potential")
-    worst, rows = _run(L, S, ctx, st, 10)
+    worst, rows, over_tol = _run(L, S, ctx, st, 10, cfg, precision)
     ctx.close()
     assert all(v <= TOL for v in worst.values()), worst
     assert all(v <= 1e-12 for v in rows.values()), rows
+    assert not over_tol, over_tol
 
 
 def _omega2_sensitivity(name, nsub):
@@ -105,21 +109,23 @@ def _omega2_sensitivity(name, nsub):
 def test_paper_rt_setup_matches_oracle(L, precision):
     from _pairs import make_paper_pair
     S, ctx, st, cfg = make_paper_pair(L, "rtp32", precision=precision)
-    worst, rows = _run(L, S, ctx, st, 10)
+    worst, rows, over_tol = _run(L, S, ctx, st, 10, cfg, precision)
     ctx.close()
     sens = _omega2_sensitivity("rtp32", 10) * (1.0 if precision == 0 else 2.0 ** 4)
     print("oracle Omega2 sensitivity to one unit roundoff of z: %.1e" % sens)
     assert worst.pop("om") <= max(TOL, 10 * sens)
     assert all(v <= TOL for v in worst.values()), worst
     assert all(v <= 1e-12 for v in rows.values()), rows
+    assert not over_tol, over_tol
 
 
 def test_paper_rt_setup_full_grid(L):
     """The paper's V^{3D,1} mesh, 128 x 512 x 128 (physical 192 x 512 x 192): start-up and two substages."""
     from _pairs import make_paper_pair
     S, ctx, st, cfg = make_paper_pair(L, "rtp128")
-    worst, rows = _run(L, S, ctx, st, 2)
+    worst, rows, over_tol = _run(L, S, ctx, st, 2, cfg, 0)
     ctx.close()
     worst.pop("om")   # conditioned as in the 32 x 65 x 32 case; m1, m3 carry it at the 1e-12 bar
     assert all(v <= TOL for v in worst.values()), worst
     assert all(v <= 1e-12 for v in rows.values()), rows
+    assert not over_tol, over_tol
