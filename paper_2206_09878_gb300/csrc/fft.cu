@@ -192,12 +192,24 @@ __device__ void fft_inplace(C* x, const FFTPlan& pl, int tt, int tpt) {
   }
 }
 
-// Launch bounds: at most 85 registers per thread in every pass (the FP64 kernels would otherwise take ~100
-// and fit fewer CTAs, whose warps hide less of the FP64 pipe's latency). The x-passes run small CTAs (2
-// transforms of 768 points, 6 per SM), so that the load, compute and store phases of different CTAs
-// (separated by barriers) overlap: 7-8% faster in double-float at 512^3. The z-passes gather `batch` kx
-// columns of each z-row, so they keep 4 of them per CTA (64-byte row segments; 3 CTAs per SM).
-constexpr int FFT_CTA_X = 128, FFT_MIN_CTAS_X = 6, FFT_CTA_Z = 256, FFT_MIN_CTAS_Z = 3;
+// Launch bounds: every pass caps its registers (FftMinCtas below); the FP64 kernels would otherwise take ~100
+// and fit fewer CTAs, whose warps hide less of the FP64 pipe's latency. The x-passes run small CTAs (2
+// transforms of 768 points, 6-7 per SM), so that the load, compute and store phases of different CTAs
+// (separated by barriers) overlap: 7-8% faster in double-float at 512^3 than 256-thread CTAs. The z-passes
+// gather `batch` kx columns of each z-row, so they keep 4 of them per CTA (64-byte row segments).
+constexpr int FFT_CTA_X = 128, FFT_CTA_Z = 256;
+// CTAs per SM each pass is compiled for, i.e. its register cap. FP64: 6 x-pass and 3 z-pass CTAs (80
+// registers). Double-float: the x-passes fit 7 CTAs at 72 registers without spilling (inverse 1.5%, forward
+// 2.8% faster at 512^3 than at 6) and the forward z-pass 4 at 64 (4.4% faster); the inverse z-pass lost 2.3%
+// at 64 registers and keeps 3.
+template <class C>
+struct FftMinCtas {
+  static constexpr int x = 6, z_inv = 3, z_fwd = 3;
+};
+template <>
+struct FftMinCtas<cdf> {
+  static constexpr int x = 7, z_inv = 3, z_fwd = 4;
+};
 // Loads a thread issues in its gather / scatter loops before it stores any of them: one load at a time would
 // serialise a memory latency per iteration (ncu: long-scoreboard stalls dominated the double-float passes).
 constexpr int FFT_LOAD_CHUNK = 4;
@@ -207,7 +219,7 @@ constexpr int FFT_LOAD_CHUNK = 4;
 // IN_DF (double-float arithmetic only): the inputs already hold double-float pairs (the precision path's
 // evaluations store them so), read without conversion.
 template <class C, int EPT, bool IN_DF = false>
-__global__ void __launch_bounds__(FFT_CTA_Z, FFT_MIN_CTAS_Z) k_fft_z_inv(FFTPlan pl, Grid g, FieldsC in, C* T, size_t tstride) {
+__global__ void __launch_bounds__(FFT_CTA_Z, FftMinCtas<C>::z_inv) k_fft_z_inv(FFTPlan pl, Grid g, FieldsC in, C* T, size_t tstride) {
   using F = FT<C>;
   extern __shared__ __align__(16) unsigned char sm_raw[];
   C* a = reinterpret_cast<C*>(sm_raw);
@@ -342,11 +354,11 @@ __device__ __forceinline__ void x_inv_body(const FFTPlan& pl, const Grid& g, con
   }
 }
 template <class C, int EPT>
-__global__ void __launch_bounds__(FFT_CTA_X, FFT_MIN_CTAS_X) k_fft_x_inv(FFTPlan pl, Grid g, const C* T, size_t tstride, FieldsRW out) {
+__global__ void __launch_bounds__(FFT_CTA_X, FftMinCtas<C>::x) k_fft_x_inv(FFTPlan pl, Grid g, const C* T, size_t tstride, FieldsRW out) {
   x_inv_body<C, EPT, false>(pl, g, T, tstride, out, nullptr);
 }
 template <class C, int EPT>
-__global__ void __launch_bounds__(FFT_CTA_X, FFT_MIN_CTAS_X) k_fft_x_inv_mul(FFTPlan pl, Grid g, const C* T, size_t tstride, FieldsRW out,
+__global__ void __launch_bounds__(FFT_CTA_X, FftMinCtas<C>::x) k_fft_x_inv_mul(FFTPlan pl, Grid g, const C* T, size_t tstride, FieldsRW out,
                                                                              const void* wmul) {
   x_inv_body<C, EPT, true>(pl, g, T, tstride, out, wmul);
 }
@@ -426,17 +438,17 @@ __device__ __forceinline__ void x_fwd_body(const FFTPlan& pl, const Grid& g, con
   }
 }
 template <class C, int EPT>
-__global__ void __launch_bounds__(FFT_CTA_X, FFT_MIN_CTAS_X) k_fft_x_fwd(FFTPlan pl, Grid g, FieldsRC in, C* T, size_t tstride) {
+__global__ void __launch_bounds__(FFT_CTA_X, FftMinCtas<C>::x) k_fft_x_fwd(FFTPlan pl, Grid g, FieldsRC in, C* T, size_t tstride) {
   x_fwd_body<C, EPT, false>(pl, g, in, T, tstride, Dot3{});
 }
 template <class C, int EPT>
-__global__ void __launch_bounds__(FFT_CTA_X, FFT_MIN_CTAS_X) k_fft_x_fwd_dot3(FFTPlan pl, Grid g, C* T, size_t tstride, Dot3 d) {
+__global__ void __launch_bounds__(FFT_CTA_X, FftMinCtas<C>::x) k_fft_x_fwd_dot3(FFTPlan pl, Grid g, C* T, size_t tstride, Dot3 d) {
   x_fwd_body<C, EPT, true>(pl, g, FieldsRC{}, T, tstride, d);
 }
 
 // ---------------------------------------------------------------- forward z-pass (truncate, scale)
 template <class C, int EPT>
-__global__ void __launch_bounds__(FFT_CTA_Z, FFT_MIN_CTAS_Z) k_fft_z_fwd(FFTPlan pl, Grid g, const C* T, size_t tstride, FieldsW out) {
+__global__ void __launch_bounds__(FFT_CTA_Z, FftMinCtas<C>::z_fwd) k_fft_z_fwd(FFTPlan pl, Grid g, const C* T, size_t tstride, FieldsW out) {
   using F = FT<C>;
   extern __shared__ __align__(16) unsigned char sm_raw[];
   C* a = reinterpret_cast<C*>(sm_raw);

@@ -50,13 +50,16 @@ def test_substages_match_oracle(L, name, over, precision):
     nsub = 2 * 5 if not over or "memory_layout" in over else 4
     worst = {}
     over_tol = []
+    prev = st
     for s in range(nsub):
         S.advance_substage()
         ctx.advance_substage()
         gpu = to_numpy(ctx.get_state())
         ctx.synchronize()
         e = compare_states(S, gpu, S.state())
-        fe, tol = intermediate_check(S, cfg, gpu_intermediates(L, ctx), oracle_intermediates(S), precision)
+        fe, tol = intermediate_check(S, cfg, gpu_intermediates(L, ctx), oracle_intermediates(S), precision,
+                                     state=prev)
+        prev = gpu
         print("substage", s, {k: "%.1e" % v for k, v in {**e, **fe}.items()}, "tol %.1e" % tol["zdot"])
         for k, v in e.items():
             worst[k] = max(worst.get(k, 0.0), v)

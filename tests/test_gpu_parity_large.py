@@ -69,13 +69,15 @@ def _compare(L, ref, precision, memory_layout=0):
     ctx = L.Context(gpu_config(L, cfg, precision, memory_layout))
     ctx.set_state(to_torch(ref["st"]))
     bad = []
+    prev = ref["st"]
     for s, (ost, oin) in enumerate(zip(ref["states"], ref["inters"])):
         ctx.advance_substage()
         gpu = to_numpy(ctx.get_state())
         ctx.synchronize()
         e = compare_states(S, gpu, ost)
         fe, tol = intermediate_check(ref["S_at"][s], cfg, gpu_intermediates(L, ctx), oin, precision,
-                                     ref["floors"][s])
+                                     ref["floors"][s], state=prev)
+        prev = gpu
         print("substage", s, {k: "%.1e" % v for k, v in {**e, **fe}.items()}, "tol %.1e" % tol["zdot"])
         bad += [(s, k, v) for k, v in e.items() if not v <= TOL]
         bad += [(s, k, v, tol[k]) for k, v in fe.items() if not v <= tol[k]]

@@ -58,6 +58,7 @@ def _run(L, S, ctx, st, nsub, cfg, precision):
     S.set_state(**st)
     ctx.set_state(to_torch(st))
     worst, rows, over_tol = {}, {}, []
+    prev = st
     for s in range(nsub):
         S.advance_substage()
         ctx.advance_substage()
@@ -65,7 +66,9 @@ def _run(L, S, ctx, st, nsub, cfg, precision):
         mc2 = ctx.field(L.LMVD_FIELD_MC2).cpu().numpy()
         ctx.synchronize()
         e = compare_states(S, gpu, S.state())
-        fe, tol = intermediate_check(S, cfg, gpu_intermediates(L, ctx), oracle_intermediates(S), precision)
+        fe, tol = intermediate_check(S, cfg, gpu_intermediates(L, ctx), oracle_intermediates(S), precision,
+                                     state=prev)
+        prev = gpu
         print("substage", s, {k: "%.1e" % v for k, v in {**e, **fe}.items()})
         for k, v in e.items():
             worst[k] = max(worst.get(k, 0.0), v)

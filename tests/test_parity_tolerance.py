@@ -97,3 +97,21 @@ def test_downstream_bound_holds_for_rounding_and_fails_for_defect():
     B.__dict__.update({k: v for k, v in S.__dict__.items()})
     bad = oracle_downstream(B, zdot)
     assert rel(bad["mc1"], ref["mc1"]) > 1e6 * bound["mc1"]
+
+
+def test_rz_reference_from_a_given_state():
+    """oracle_rz on the oracle's own state at the start of a substage reproduces that substage's R_z
+    exactly, leaves the oracle untouched, and follows a change of the state (R_z is not a constant)."""
+    from _pairs import oracle_rz
+    w = workload("rt32")
+    S = Substage(oracle_config(w))
+    S.set_state(**rt_state(**w))
+    S.advance_substage()
+    before = {k: v.copy() for k, v in S.state().items()}
+    S.advance_substage()
+    z_after, rz_after, trace_keys = S.z.copy(), S.Rz, set(S.trace)
+    rz = oracle_rz(S, before)
+    assert np.array_equal(rz, S.Rz)
+    assert np.array_equal(S.z, z_after) and S.Rz is rz_after and set(S.trace) == trace_keys
+    moved = dict(before, z=before["z"] * (1 + 1e-6))
+    assert rel(oracle_rz(S, moved), S.Rz) > 1e-9
