@@ -294,6 +294,21 @@ def traffic_per_launch(fp, kernel, grid, alg_bytes_per_launch):
     return frac * alg_bytes_per_launch
 
 
+def class_table(prof, steps):
+    """Per kernel class and step: time, launches, algorithmic TFLOP/s and GB/s, and the GB/s as a fraction
+    of the measured HBM copy bandwidth (prof: class -> (ms, launches, flops, bytes) over `steps` steps)."""
+    peak = hbm_peak_gbs()[0]
+    out = {}
+    for k, (ms, n, fl, by) in prof.items():
+        if n <= 0:
+            continue
+        gbs = by / (ms / 1e3) / 1e9 if ms > 0 else None
+        out[k] = {"ms_per_step": ms / steps, "launches_per_step": n / steps,
+                  "tflops": fl / (ms / 1e3) / 1e12 if ms > 0 else None,
+                  "hbm_gbs": gbs, "hbm_frac": gbs / peak if gbs is not None else None}
+    return out
+
+
 def measured_rates(L, iters=4000):
     """Issue rates of this GPU from the library's probe (lmvd_rate_probe): FP64 FMA / add / multiply and
     FP32 FMA, operations per second (8 independent chains per thread, 8 CTAs of 256 per SM). The FP32 probe
@@ -574,11 +589,7 @@ def run_cuda(args):
     res, final = time_variant(L, w, args.precision, args, stream, st, local, ws, e2e_steps=args.e2e_steps)
     ms_max, value = aggregate(res["ms"], npts * args.steps, ws, device="cuda")
     prof = res["prof"]
-    breakdown = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps,
-                     "tflops": (v[2] / (v[0] / 1e3) / 1e12) if v[0] > 0 else None,
-                     "hbm_gbs": (v[3] / (v[0] / 1e3) / 1e9) if v[0] > 0 else None,
-                     "hbm_frac": (v[3] / (v[0] / 1e3) / 1e9 / hbm_peak_gbs()[0]) if v[0] > 0 else None}
-                 for k, v in prof.items() if v[1] > 0}
+    breakdown = class_table(prof, args.steps)
     e2e = None
     if args.e2e_steps > 0:
         e2e_value = aggregate(1e3 * res["e2e_s"], npts * args.e2e_steps, ws, device="cuda")[1]
@@ -608,9 +619,7 @@ def run_cuda(args):
             "value": v2, "unit": UNIT, "ms_per_step": r2["ms"] / args.steps, "clocks": r2["clocks"],
             "device_bytes": r2["device_bytes"],
             "roofline": roofline_of(r2["prof"], r2["ms"], other, (w["nx"], w["ny"], w["nz"]), rates),
-            "kernels": {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps,
-                            "tflops": (v[2] / (v[0] / 1e3) / 1e12) if v[0] > 0 else None}
-                        for k, v in r2["prof"].items() if v[1] > 0},
+            "kernels": class_table(r2["prof"], args.steps),
             "state_rel_l2_vs_headline_after_%d_substages" % (args.warmup + args.steps): errs,
         }
     if rank == 0 and ws == 1 and not args.no_cufft:

@@ -42,3 +42,16 @@ def test_measured_rates_set_the_peaks():
     assert r["peak"] == pytest.approx(1.2) and "measured" in r["peak_note"]
     rd = bench.roofline_of(prof, 400.0, 1, (512, 513, 512), rates)
     assert rd["peak"] == pytest.approx(4.0) and rd["frac"] == pytest.approx(rd["achieved"] / 4.0)
+
+
+def test_class_table_rates():
+    """Per-class table: ms and launches per step, algorithmic TFLOP/s and GB/s, fraction of the copy peak."""
+    import bench
+    prof = {"products": (20.0, 4.0, 1e12, 8e10), "idle": (0.0, 0.0, 0.0, 0.0)}
+    t = bench.class_table(prof, 2)
+    assert set(t) == {"products"}
+    r = t["products"]
+    assert r["ms_per_step"] == 10.0 and r["launches_per_step"] == 2.0
+    assert r["tflops"] == pytest.approx(1e12 / 0.02 / 1e12)
+    assert r["hbm_gbs"] == pytest.approx(8e10 / 0.02 / 1e9)
+    assert r["hbm_frac"] == pytest.approx(r["hbm_gbs"] / bench.hbm_peak_gbs()[0])
