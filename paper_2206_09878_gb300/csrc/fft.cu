@@ -7,8 +7,10 @@
 // (kx < nx/2 only -- the padded kx range carries zeros and is never stored):
 //   inverse: z-pass (complex, length pz, zero-padded in kz) then x-pass (complex-to-real, length px,
 //            two real rows packed into one complex transform);
-//   forward: x-pass (real-to-complex, two rows per complex transform, split by Hermitian symmetry)
-//            then z-pass (complex, truncated, scaled by 1/(px pz)).
+//   forward: x-pass (real-to-complex, two rows per complex transform, split by Hermitian symmetry; the
+//            split's factor 1/2 is left to the z-pass) then z-pass (complex, truncated, scaled by
+//            1/(2 px pz), which is bit-for-bit the same as halving first: power-of-two scaling commutes
+//            with every rounding of the pass).
 // Synthesis is unnormalised: f(x, z) = sum_k fhat_k exp(i (k1 x + k3 z)).
 // A pass is one CTA per (plane, field, batch of columns / row pairs); every 1D transform is a
 // Stockham autosort FFT in shared memory with radix-4/3/2 stages and a precomputed twiddle table.
@@ -475,8 +477,9 @@ __device__ __forceinline__ void x_fwd_body(const FFTPlan& pl, const Grid& g, con
     if (!LMVD_IN((size_t)za * h + k, (size_t)pz * h) || !LMVD_IN(bb * ld + px - 1, batch * ld)) continue;
     const C yk = res[bb * ld + k];
     const C ym = F::cj(res[bb * ld + (k == 0 ? 0 : px - k)]);
-    dst[(size_t)za * h + k] = F::half(F::add(yk, ym));
-    if (zb < pz) dst[(size_t)zb * h + k] = F::neg(F::ti(F::half(F::sub(yk, ym))));  // (yk - ym) / (2 i)
+    // twice the two rows' spectra (the 1/2 is in the z-pass's scale): yk + ym and (yk - ym) / i
+    dst[(size_t)za * h + k] = F::add(yk, ym);
+    if (zb < pz) dst[(size_t)zb * h + k] = F::neg(F::ti(F::sub(yk, ym)));
   }
 }
 template <class C, int EPT>
@@ -611,8 +614,8 @@ int fft_prepare(Ctx& c) {
     if (cudaMemcpy(p->tw, tw.data(), sizeof(double2) * p->n, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(p->twf, twf.data(), sizeof(float4) * p->n, cudaMemcpyHostToDevice) != cudaSuccess)
       return LMVD_ERR_CUDA;
-    p->scale_d = (double)scale;
-    p->scale_f = host_split(scale);
+    p->scale_d = (double)(scale / 2);  // used by the forward z-pass (see the file head)
+    p->scale_f = host_split(scale / 2);
     p->s3f = host_split(sqrtl(3.0L) / 2.0L);
   }
   int e = set_smem<cd>(c.fx, c.fz);

@@ -176,7 +176,7 @@ struct FFTPlan {
   int ept = 12;            // elements per thread (a multiple of every radix of the plan)
   int tpt = 1;             // threads per transform = n / ept; a CTA has tpt * batch threads
   int pad = 1;             // shared-memory leading dimension of a transform: n + pad
-  double scale_d = 1.0;    // 1 / (px pz) for the forward z-pass
+  double scale_d = 1.0;    // 1 / (2 px pz) for the forward z-pass (with the x-pass's 1/2)
   df scale_f{1.f, 0.f};
   df s3f{0.f, 0.f};        // sin(2 pi / 3) as a double-float
 };
