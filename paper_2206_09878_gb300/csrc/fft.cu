@@ -19,6 +19,8 @@
 // by the complex type C. Spectral inputs and outputs are always complex double; the intermediate
 // T and the physical fields are stored in the arithmetic's own type (double, or hi/lo float pairs
 // of the same size), so the double-float path converts only at the spectral ends.
+#include <cuda.h>  // CUtensorMap and its enums (the encoder is reached through the runtime, no libcuda link)
+
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -129,7 +131,9 @@ struct FT<cdf> {
 // a synthesis), so their loads and the additions with them are skipped. SKIP (a last stage): outputs at
 // positions [lo, hi) are not wanted (the truncated modes of an analysis), so their additions and stores
 // are skipped.
-template <class C, int SIGN, int R, int EPT, bool ZERO = false, bool SKIP = false>
+// S: distance in elements between consecutive points of a transform in shared memory (1: contiguous; the
+// z-passes interleave their columns, point i of column c at (i S + c)).
+template <class C, int SIGN, int R, int EPT, bool ZERO = false, bool SKIP = false, int S = 1>
 __device__ __forceinline__ void fft_stage(C* x, const FFTPlan& pl, int L, int tt, int tpt, int lo = 0, int hi = 0) {
   using F = FT<C>;
   static_assert(!ZERO || R == 4, "zero-input pruning is written for a first radix-4 stage");
@@ -146,7 +150,7 @@ __device__ __forceinline__ void fft_stage(C* x, const FFTPlan& pl, int L, int tt
       const int i = b + q * nb;
       bool ld = LMVD_IN(i, n);
       if constexpr (ZERO) ld = ld && (i < lo || i >= hi);
-      v[j][q] = ld ? x[i] : FT<C>::zero();
+      v[j][q] = ld ? x[i * S] : FT<C>::zero();
     }
   }
   __syncthreads();
@@ -180,31 +184,31 @@ __device__ __forceinline__ void fft_stage(C* x, const FFTPlan& pl, int L, int tt
         d3 = F::ti(F::sub_lazy(v[j][1], v[j][3]));
       }
       const C t3 = SIGN > 0 ? d3 : F::neg(d3);  // (SIGN i) (v1 - v3)
-      if (want(0)) x[base] = F::add(t0, t2);
-      if (want(1)) x[base + L] = F::add(t1, t3);
-      if (want(2)) x[base + 2 * L] = F::sub(t0, t2);
-      if (want(3)) x[base + 3 * L] = F::sub(t1, t3);
+      if (want(0)) x[base * S] = F::add(t0, t2);
+      if (want(1)) x[(base + L) * S] = F::add(t1, t3);
+      if (want(2)) x[(base + 2 * L) * S] = F::sub(t0, t2);
+      if (want(3)) x[(base + 3 * L) * S] = F::sub(t1, t3);
     } else if (R == 3) {
       const C t1 = F::add_lazy(v[j][1], v[j][2]);
       const C m = F::sub_lazy(v[j][0], F::half(t1));
       const C u = F::ti(F::template mul_s3<SIGN>(F::sub_lazy(v[j][1], v[j][2]), pl));
-      if (want(0)) x[base] = F::add(v[j][0], t1);
-      if (want(1)) x[base + L] = F::add(m, u);
-      if (want(2)) x[base + 2 * L] = F::sub(m, u);
+      if (want(0)) x[base * S] = F::add(v[j][0], t1);
+      if (want(1)) x[(base + L) * S] = F::add(m, u);
+      if (want(2)) x[(base + 2 * L) * S] = F::sub(m, u);
     } else {
-      if (want(0)) x[base] = F::add(v[j][0], v[j][1]);
-      if (want(1)) x[base + L] = F::sub(v[j][0], v[j][1]);
+      if (want(0)) x[base * S] = F::add(v[j][0], v[j][1]);
+      if (want(1)) x[(base + L) * S] = F::sub(v[j][0], v[j][1]);
     }
   }
   __syncthreads();
 }
 
-template <class C, int SIGN, int EPT, bool SKIP>
+template <class C, int SIGN, int EPT, bool SKIP, int S>
 __device__ __forceinline__ void fft_stage_r(unsigned r2, C* x, const FFTPlan& pl, int L, int tt, int tpt, int lo,
                                             int hi) {
-  if (r2 == 0) fft_stage<C, SIGN, 4, EPT, false, SKIP>(x, pl, L, tt, tpt, lo, hi);
-  else if (r2 == 2) fft_stage<C, SIGN, 3, EPT, false, SKIP>(x, pl, L, tt, tpt, lo, hi);
-  else fft_stage<C, SIGN, 2, EPT, false, SKIP>(x, pl, L, tt, tpt, lo, hi);
+  if (r2 == 0) fft_stage<C, SIGN, 4, EPT, false, SKIP, S>(x, pl, L, tt, tpt, lo, hi);
+  else if (r2 == 2) fft_stage<C, SIGN, 3, EPT, false, SKIP, S>(x, pl, L, tt, tpt, lo, hi);
+  else fft_stage<C, SIGN, 2, EPT, false, SKIP, S>(x, pl, L, tt, tpt, lo, hi);
 }
 
 // All stages of one transform held at x (the caller has synchronised after filling x).
@@ -213,12 +217,12 @@ __device__ __forceinline__ void fft_stage_r(unsigned r2, C* x, const FFTPlan& pl
 // output are not wanted (pruned in the last stage). Compile-time switches, so that a pass without pruning
 // compiles to the plain stages. The FP64 passes prune (synthesis 7%, analysis <1% faster at 512^3); the
 // double-float ones do not (their x-passes spilled at the 72-register cap and lost 6%).
-template <class C, int SIGN, int EPT, bool PZ = false, bool PS = false>
+template <class C, int SIGN, int EPT, bool PZ = false, bool PS = false, int S = 1>
 __device__ void fft_inplace(C* x, const FFTPlan& pl, int tt, int tpt, int lo = 0, int hi = 0) {
   int L = 1, s = 0;
   unsigned code = pl.code;
   if (PZ && lo < hi && (code & 3u) == 0 && pl.nst > 1) {
-    fft_stage<C, SIGN, 4, EPT, true, false>(x, pl, 1, tt, tpt, lo, hi);
+    fft_stage<C, SIGN, 4, EPT, true, false, S>(x, pl, 1, tt, tpt, lo, hi);
     L = 4;
     s = 1;
     code >>= 2;
@@ -226,10 +230,10 @@ __device__ void fft_inplace(C* x, const FFTPlan& pl, int tt, int tpt, int lo = 0
   const int last = PS && lo < hi ? pl.nst - 1 : pl.nst;
   for (; s < last; ++s, code >>= 2) {
     const unsigned r2 = code & 3u;
-    fft_stage_r<C, SIGN, EPT, false>(r2, x, pl, L, tt, tpt, 0, 0);
+    fft_stage_r<C, SIGN, EPT, false, S>(r2, x, pl, L, tt, tpt, 0, 0);
     L *= r2 == 0 ? 4 : (r2 == 2 ? 3 : 2);
   }
-  if (PS && s < pl.nst) fft_stage_r<C, SIGN, EPT, true>(code & 3u, x, pl, L, tt, tpt, lo, hi);
+  if (PS && s < pl.nst) fft_stage_r<C, SIGN, EPT, true, S>(code & 3u, x, pl, L, tt, tpt, lo, hi);
 }
 
 // The passes that prune (see fft_inplace).
@@ -258,51 +262,104 @@ struct FftMinCtas<cdf> {
 // serialise a memory latency per iteration (ncu: long-scoreboard stalls dominated the double-float passes).
 constexpr int FFT_LOAD_CHUNK = 4;
 
+// ---------------------------------------------------------------- tile loads (TMA)
+// The z-passes read columns of a row-major plane: batch consecutive kx (16-byte elements) of every z-row. A
+// tensor-map tile copy (cp.async.bulk.tensor) fetches such a box (2 batch doubles x rows) into shared
+// memory as one asynchronous operation completing on an mbarrier, instead of one 16-byte load per thread
+// and element. The box lands row-major, i.e. as the interleaved layout the z-pass transforms work in.
+struct ZMaps {
+  CUtensorMap m[TBUF_FIELDS];  // one per field of the launch (z_inv: the spectral inputs; z_fwd: m[0] = T)
+};
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// box of the 3D map at (x, y, z) (x in doubles) into dst; completes tx bytes on bar
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z,
+                                            unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+      ::"r"(smem_addr(dst)), "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
+      : "memory");
+}
+
+// Every thread waits for phase 0 of bar, for at most ~1 s of SM clock; false (and bit 2 of the context's
+// status word, when there is one) if the copies did not complete by then.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned* flags) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, 0)) {
+    if (clock64() - t0 > 2000000000ll) {
+      if (flags && threadIdx.x == 0) atomicOr(flags, 4u);
+      return false;
+    }
+  }
+  return true;
+}
+
 // ---------------------------------------------------------------- inverse z-pass
 // in: spectral value fields [ny][nz][nxh] (complex double); T: [f][ny][pz][nx/2] of C
 // IN_DF (double-float arithmetic only): the inputs already hold double-float pairs (the precision path's
 // evaluations store them so), read without conversion.
-template <class C, int EPT, bool IN_DF = false>
-__global__ void __launch_bounds__(FFT_CTA_Z, FftMinCtas<C>::z_inv) k_fft_z_inv(FFTPlan pl, Grid g, FieldsC in, C* T, size_t tstride) {
+// A CTA transforms COLS kx columns of one plane. Shared layout: point z of column c at a[z COLS + c]; two
+// tile loads per row block put the kz >= 0 rows at the top and the kz < 0 rows at the bottom of the padded
+// column (the Nyquist row lands inside the zero band, which the FP64 passes never read and the double-float
+// ones clear).
+template <class C, int EPT, int COLS, bool IN_DF = false>
+__global__ void __launch_bounds__(FFT_CTA_Z, FftMinCtas<C>::z_inv)
+    k_fft_z_inv(FFTPlan pl, Grid g, const __grid_constant__ ZMaps maps, C* T, size_t tstride, unsigned* flags) {
   using F = FT<C>;
-  extern __shared__ __align__(16) unsigned char sm_raw[];
+  extern __shared__ __align__(128) unsigned char sm_raw[];
   C* a = reinterpret_cast<C*>(sm_raw);
-  const int batch = pl.batch, ld = pl.n + pl.pad, pz = g.pz, nz = g.nz, h = g.nx / 2;
-  const int kx0 = blockIdx.x * batch, j = blockIdx.y, f = blockIdx.z;
-  const int bt = threadIdx.x / pl.tpt, tt = threadIdx.x - bt * pl.tpt;
-  for (int idx = threadIdx.x; idx < batch * ld; idx += blockDim.x) a[idx] = F::zero();
+  const int pz = g.pz, nz = g.nz, h = g.nx / 2, n2 = nz / 2, H = pl.rows_in;
+  const int kx0 = blockIdx.x * COLS, j = blockIdx.y, f = blockIdx.z;
+  const int c = threadIdx.x % COLS, tt = threadIdx.x / COLS;
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(sm_raw + (size_t)pz * COLS * sizeof(C));
+  if (threadIdx.x == 0) mbar_init(bar);
   __syncthreads();
-  const cd* src = pick(in.p, f) + (size_t)j * g.M;
-  for (int base = threadIdx.x; base < nz * batch; base += FFT_LOAD_CHUNK * blockDim.x) {
-    C v[FFT_LOAD_CHUNK];
-    int d[FFT_LOAD_CHUNK];
-#pragma unroll
-    for (int u = 0; u < FFT_LOAD_CHUNK; ++u) {
-      const int idx = base + u * blockDim.x;
-      d[u] = -1;
-      if (idx >= nz * batch) continue;
-      const int jz = idx / batch, bb = idx - jz * batch, kx = kx0 + bb;
-      if (kx < h && jz != nz / 2) {
-        const int pos = jz < nz / 2 ? jz : pz - nz + jz;
-        if (LMVD_IN(bb * ld + pos, batch * ld) && LMVD_IN((size_t)jz * g.nxh + kx, g.M)) {
-          d[u] = bb * ld + pos;
-          if constexpr (IN_DF) v[u] = reinterpret_cast<const C*>(src)[(size_t)jz * g.nxh + kx];
-          else v[u] = F::from_spec(src[(size_t)jz * g.nxh + kx]);
-        }
+  if (threadIdx.x == 0 && LMVD_IN(f, TBUF_FIELDS)) {
+    mbar_expect_tx(bar, (unsigned)(nz * COLS * sizeof(C)));
+    for (int r = 0; r < nz; r += H) {
+      const int pos = r < n2 ? r : pz - nz + r;
+      if (LMVD_IN((pos + H) * COLS - 1, pz * COLS)) tma_load_3d(a + (size_t)pos * COLS, &maps.m[f], 2 * kx0, r, j, bar);
+    }
+  }
+  if (!mbar_wait_bounded(bar, flags)) return;
+  constexpr bool convert = !IN_DF && !std::is_same<C, cd>::value;
+  if constexpr (!kPrune<C> || convert) {
+    // the padding band [n2, pz - n2 + 1) zeroed where the arithmetic reads it; spectral doubles to pairs
+    for (int idx = threadIdx.x; idx < pz * COLS; idx += blockDim.x) {
+      const int z = idx / COLS;
+      if (z >= n2 && z < pz - n2 + 1) {
+        if (!kPrune<C>) a[idx] = F::zero();
+      } else if (convert) {
+        a[idx] = F::from_spec(reinterpret_cast<const cd*>(a)[idx]);
       }
     }
-#pragma unroll
-    for (int u = 0; u < FFT_LOAD_CHUNK; ++u)
-      if (d[u] >= 0) a[d[u]] = v[u];
+    __syncthreads();
   }
-  __syncthreads();
-  fft_inplace<C, 1, EPT, kPrune<C>, false>(a + bt * ld, pl, tt, pl.tpt, nz / 2, pz - nz / 2 + 1);  // kz padding: zero
-  const C* res = a;
+  fft_inplace<C, 1, EPT, kPrune<C>, false, COLS>(a + c, pl, tt, pl.tpt, n2, pz - n2 + 1);  // kz padding: zero
   C* dst = T + f * tstride + (size_t)j * pz * h;
-  for (int idx = threadIdx.x; idx < pz * batch; idx += blockDim.x) {
-    const int zz = idx / batch, bb = idx - zz * batch, kx = kx0 + bb;
-    if (kx < h && LMVD_IN((size_t)zz * h + kx, (size_t)pz * h) && LMVD_IN(bb * ld + zz, batch * ld))
-      dst[(size_t)zz * h + kx] = res[bb * ld + zz];
+  for (int idx = threadIdx.x; idx < pz * COLS; idx += blockDim.x) {
+    const int zz = idx / COLS, kx = kx0 + idx % COLS;
+    if (kx < h && LMVD_IN((size_t)zz * h + kx, (size_t)pz * h)) dst[(size_t)zz * h + kx] = a[idx];
   }
 }
 
@@ -315,7 +372,7 @@ __device__ __forceinline__ void x_inv_body(const FFTPlan& pl, const Grid& g, con
                                            const FieldsRW& out, const void* wmul) {
   using F = FT<C>;
   using R = typename F::R;
-  extern __shared__ __align__(16) unsigned char sm_raw[];
+  extern __shared__ __align__(128) unsigned char sm_raw[];
   C* a = reinterpret_cast<C*>(sm_raw);
   const int batch = pl.batch, ld = pl.n + pl.pad, px = g.px, pz = g.pz, h = g.nx / 2;
   const int pr0 = blockIdx.x * batch, j = blockIdx.y, f = blockIdx.z;
@@ -420,7 +477,7 @@ __device__ __forceinline__ void x_fwd_body(const FFTPlan& pl, const Grid& g, con
                                            const Dot3& d) {
   using F = FT<C>;
   using R = typename F::R;
-  extern __shared__ __align__(16) unsigned char sm_raw[];
+  extern __shared__ __align__(128) unsigned char sm_raw[];
   C* a = reinterpret_cast<C*>(sm_raw);
   const int batch = pl.batch, ld = pl.n + pl.pad, px = g.px, pz = g.pz, h = g.nx / 2;
   const int pr0 = blockIdx.x * batch, j = blockIdx.y, f = blockIdx.z;
@@ -492,42 +549,35 @@ __global__ void __launch_bounds__(FFT_CTA_X, FftMinCtas<C>::x) k_fft_x_fwd_dot3(
 }
 
 // ---------------------------------------------------------------- forward z-pass (truncate, scale)
-template <class C, int EPT>
-__global__ void __launch_bounds__(FFT_CTA_Z, FftMinCtas<C>::z_fwd) k_fft_z_fwd(FFTPlan pl, Grid g, const C* T, size_t tstride, FieldsW out) {
+// T: [f][ny][pz][nx/2] of C, read through maps.m[0] (all fields of the launch: planes f ny + j); out:
+// spectral fields [ny][nz][nxh]. Same interleaved layout as the inverse z-pass; kx = nx/2 and the kz
+// Nyquist row are written as zero.
+template <class C, int EPT, int COLS>
+__global__ void __launch_bounds__(FFT_CTA_Z, FftMinCtas<C>::z_fwd)
+    k_fft_z_fwd(FFTPlan pl, Grid g, const __grid_constant__ ZMaps maps, FieldsW out, unsigned* flags) {
   using F = FT<C>;
-  extern __shared__ __align__(16) unsigned char sm_raw[];
+  extern __shared__ __align__(128) unsigned char sm_raw[];
   C* a = reinterpret_cast<C*>(sm_raw);
-  const int batch = pl.batch, ld = pl.n + pl.pad, pz = g.pz, nz = g.nz, h = g.nx / 2;
-  const int kx0 = blockIdx.x * batch, j = blockIdx.y, f = blockIdx.z;
-  const int bt = threadIdx.x / pl.tpt, tt = threadIdx.x - bt * pl.tpt;
-  const C* src = T + f * tstride + (size_t)j * pz * h;
-  for (int base = threadIdx.x; base < pz * batch; base += FFT_LOAD_CHUNK * blockDim.x) {
-    C v[FFT_LOAD_CHUNK];
-    int d[FFT_LOAD_CHUNK];
-#pragma unroll
-    for (int u = 0; u < FFT_LOAD_CHUNK; ++u) {
-      const int idx = base + u * blockDim.x;
-      d[u] = -1;
-      if (idx >= pz * batch) continue;
-      const int zz = idx / batch, bb = idx - zz * batch, kx = kx0 + bb;
-      if (!LMVD_IN(bb * ld + zz, batch * ld)) continue;
-      d[u] = bb * ld + zz;
-      v[u] = (kx < h && LMVD_IN((size_t)zz * h + kx, (size_t)pz * h)) ? src[(size_t)zz * h + kx] : F::zero();
-    }
-#pragma unroll
-    for (int u = 0; u < FFT_LOAD_CHUNK; ++u)
-      if (d[u] >= 0) a[d[u]] = v[u];
-  }
+  const int pz = g.pz, nz = g.nz, h = g.nx / 2, n2 = nz / 2, H = pl.rows_t;
+  const int kx0 = blockIdx.x * COLS, j = blockIdx.y, f = blockIdx.z;
+  const int c = threadIdx.x % COLS, tt = threadIdx.x / COLS;
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(sm_raw + (size_t)pz * COLS * sizeof(C));
+  if (threadIdx.x == 0) mbar_init(bar);
   __syncthreads();
-  fft_inplace<C, -1, EPT, false, kPrune<C>>(a + bt * ld, pl, tt, pl.tpt, nz / 2, pz - nz / 2 + 1);  // truncated kz
-  const C* res = a;
+  if (threadIdx.x == 0) {
+    mbar_expect_tx(bar, (unsigned)(pz * COLS * sizeof(C)));
+    for (int r = 0; r < pz; r += H)
+      if (LMVD_IN((r + H) * COLS - 1, pz * COLS)) tma_load_3d(a + (size_t)r * COLS, &maps.m[0], 2 * kx0, r, f * g.ny + j, bar);
+  }
+  if (!mbar_wait_bounded(bar, flags)) return;
+  fft_inplace<C, -1, EPT, false, kPrune<C>, COLS>(a + c, pl, tt, pl.tpt, n2, pz - n2 + 1);  // truncated kz
   cd* dst = pick(out.p, f) + (size_t)j * g.M;
-  for (int idx = threadIdx.x; idx < nz * batch; idx += blockDim.x) {
-    const int jz = idx / batch, bb = idx - jz * batch, kx = kx0 + bb;
+  for (int idx = threadIdx.x; idx < nz * COLS; idx += blockDim.x) {
+    const int jz = idx / COLS, cc = idx % COLS, kx = kx0 + cc;
     if (kx > h) continue;
+    const int pos = jz < n2 ? jz : pz - nz + jz;
     cd v = mk(0, 0);
-    if (kx < h && jz != nz / 2 && LMVD_IN(bb * ld + (jz < nz / 2 ? jz : pz - nz + jz), batch * ld))
-      v = F::to_spec(res[bb * ld + (jz < nz / 2 ? jz : pz - nz + jz)], pl);
+    if (kx < h && jz != n2 && LMVD_IN(pos * COLS + cc, pz * COLS)) v = F::to_spec(a[pos * COLS + cc], pl);
     if (LMVD_IN((size_t)jz * g.nxh + kx, g.M)) dst[(size_t)jz * g.nxh + kx] = v;
   }
 }
@@ -552,15 +602,60 @@ static bool make_plan(int n, int cta, FFTPlan& p) {
   p.tpt = n / p.ept;
   if (p.tpt > cta) return false;
   p.batch = cta / p.tpt;
-  // leading dimension n + pad of a transform in shared memory. The z-passes gather and scatter their batch of
-  // columns with the column index fastest across threads: with n + 2 the 16-byte elements of four columns at
-  // the same position land in distinct bank groups (n + 1 put neighbouring positions of adjacent columns in
-  // the same one: 2-way conflicts). The x-passes walk one transform contiguously and keep n + 1.
-  p.pad = cta == FFT_CTA_Z ? 2 : 1;
+  p.pad = 1;  // the x-passes: leading dimension n + 1 keeps the transforms of a batch in different banks
+  if (cta == FFT_CTA_Z) {
+    // the z-passes: 4 interleaved columns per CTA (2 when 4 transforms of n do not fit in cta threads; the
+    // 6-element plans exist only for 4), and tile copies whose rows divide their range and start on 128-byte
+    // boundaries in shared memory (rows x batch x 16 bytes a multiple of 128)
+    p.batch = 4 * p.tpt <= cta ? 4 : (p.ept == 12 && 2 * p.tpt <= cta ? 2 : 0);
+    if (!p.batch || n % 3) return false;
+    p.pad = 0;
+    auto rows = [&](int total) {
+      for (int r = total < 256 ? total : 256; r > 0; --r)
+        if (total % r == 0 && (r * p.batch) % 8 == 0) return r;
+      return 0;
+    };
+    p.rows_in = rows(n / 3);  // nz / 2 = pz / 3
+    p.rows_t = rows(n);
+    if (!p.rows_in || !p.rows_t) return false;
+  }
   return true;
 }
 
-static size_t smem_bytes(const FFTPlan& p) { return (size_t)p.batch * (p.n + p.pad) * sizeof(cd); }
+// the z-passes' buffer is followed by their mbarrier
+static size_t smem_bytes(const FFTPlan& p) { return (size_t)p.batch * (p.n + p.pad) * sizeof(cd) + (p.rows_t ? 16 : 0); }
+
+// Tensor maps for the z-passes' tile copies. cuTensorMapEncodeTiled is a driver function; the runtime hands
+// out its address, so the library needs no link to the driver library.
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  });
+  return fn;
+}
+
+// A map over planes x rows x cols 16-byte elements at base (row-major, contiguous), addressed in doubles:
+// boxes of (2 bcols doubles, brows rows, 1 plane); out-of-range parts of a box read as zero.
+static bool tile_map(CUtensorMap* m, const void* base, size_t cols, size_t rows, size_t planes, int bcols, int brows) {
+  const EncodeTiledFn fn = encode_tiled();
+  if (!fn || !base || ((uintptr_t)base & 15)) return false;
+  const cuuint64_t dims[3] = {2 * (cuuint64_t)cols, (cuuint64_t)rows, (cuuint64_t)planes};
+  const cuuint64_t strides[2] = {16 * (cuuint64_t)cols, 16 * (cuuint64_t)cols * rows};
+  const cuuint32_t box[3] = {(cuuint32_t)(2 * bcols), (cuuint32_t)brows, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, const_cast<void*>(base), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
 static unsigned threads(const FFTPlan& p) { return (unsigned)(p.batch * p.tpt); }
 
 static df host_split(long double x) {
@@ -568,10 +663,31 @@ static df host_split(long double x) {
   return df{h, (float)(x - (long double)h)};
 }
 
+// Every pass may take up to kFftSmemMax bytes of dynamic shared memory. The limit is a property of the
+// kernel, shared by all contexts and the allocation-free path in the process: setting it to one grid's size
+// would break the launches of another context with a larger grid, so it is set once, to the maximum a plan
+// may ask for (fft_prepare rejects larger plans).
+constexpr int kFftSmemMax = 200 * 1024;
+
+template <class C, int EPT, int COLS>
+static int set_smem_z(int sz) {
+  if (cudaFuncSetAttribute(k_fft_z_inv<C, EPT, COLS>, cudaFuncAttributeMaxDynamicSharedMemorySize, sz) != cudaSuccess ||
+      cudaFuncSetAttribute(k_fft_z_fwd<C, EPT, COLS>, cudaFuncAttributeMaxDynamicSharedMemorySize, sz) != cudaSuccess)
+    return LMVD_ERR_CUDA;
+  if constexpr (std::is_same<C, cdf>::value) {
+    if (cudaFuncSetAttribute(k_fft_z_inv<C, EPT, COLS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sz) !=
+        cudaSuccess)
+      return LMVD_ERR_CUDA;
+  }
+  return LMVD_OK;
+}
+
 template <class C, int EPT>
 static int set_smem_e(int sx, int sz) {
-  if (cudaFuncSetAttribute(k_fft_z_inv<C, EPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, sz) != cudaSuccess ||
-      cudaFuncSetAttribute(k_fft_z_fwd<C, EPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, sz) != cudaSuccess ||
+  if constexpr (EPT == 12) {
+    if (set_smem_z<C, EPT, 2>(sz)) return LMVD_ERR_CUDA;
+  }
+  if (set_smem_z<C, EPT, 4>(sz) ||
       cudaFuncSetAttribute(k_fft_x_inv<C, EPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, sx) != cudaSuccess ||
       cudaFuncSetAttribute(k_fft_x_fwd<C, EPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, sx) != cudaSuccess ||
       cudaFuncSetAttribute(k_fft_x_inv_mul<C, EPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, sx) != cudaSuccess ||
@@ -581,13 +697,9 @@ static int set_smem_e(int sx, int sz) {
 }
 
 template <class C>
-static int set_smem(const FFTPlan& fx, const FFTPlan& fz) {
-  const int sx = (int)smem_bytes(fx), sz = (int)smem_bytes(fz);
-  int e = set_smem_e<C, 12>(sx, sz);
-  if (!e) e = set_smem_e<C, 6>(sx, sz);
-  if (!e && (cudaFuncSetAttribute(k_fft_z_inv<cdf, 12, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sz) != cudaSuccess ||
-             cudaFuncSetAttribute(k_fft_z_inv<cdf, 6, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sz) != cudaSuccess))
-    e = LMVD_ERR_CUDA;
+static int set_smem() {
+  int e = set_smem_e<C, 12>(kFftSmemMax, kFftSmemMax);
+  if (!e) e = set_smem_e<C, 6>(kFftSmemMax, kFftSmemMax);
   return e;
 }
 
@@ -596,7 +708,7 @@ int fft_prepare(Ctx& c) {
   const long double scale = 1.0L / ((long double)c.g.px * (long double)c.g.pz);
   const long double pi = 3.141592653589793238462643383279502884L;
   for (FFTPlan* p : {&c.fx, &c.fz}) {
-    if (smem_bytes(*p) > 200 * 1024) return LMVD_ERR_UNSUPPORTED;
+    if (smem_bytes(*p) > kFftSmemMax) return LMVD_ERR_UNSUPPORTED;
     std::vector<double2> tw(p->n);
     std::vector<float4> twf(p->n);
     for (int m = 0; m < p->n; ++m) {
@@ -618,14 +730,64 @@ int fft_prepare(Ctx& c) {
     p->scale_f = host_split(scale / 2);
     p->s3f = host_split(sqrtl(3.0L) / 2.0L);
   }
-  int e = set_smem<cd>(c.fx, c.fz);
-  if (!e) e = set_smem<cdf>(c.fx, c.fz);
+  int e = set_smem<cd>();
+  if (!e) e = set_smem<cdf>();
   return e;
 }
 
 static inline unsigned cdiv(unsigned a, unsigned b) { return (a + b - 1) / b; }
 // conventional algorithmic flop count of one complex transform of length n: 5 n log2 n
 static inline double fft_flops(double n) { return 5.0 * n * std::log2(n); }
+
+// A tensor map that could not be encoded: the context's status becomes LMVD_ERR_CUDA (unless one is set).
+static void map_failed(Ctx& c) {
+  if (c.status == LMVD_OK) c.status = LMVD_ERR_CUDA;
+}
+
+// The inverse z-pass of n fields (spectral inputs fi) into T, and the forward z-pass of n fields of T into
+// fo: tensor maps for their tile copies, then one launch of the instantiation the plan selects.
+template <class C, bool IN_DF>
+static void z_inv_launch(Ctx& c, const FieldsC& fi, int n, C* T, size_t tstride, double fl, double by) {
+  const Grid& g = c.g;
+  const FFTPlan& p = c.fz;
+  ZMaps maps;
+  for (int f = 0; f < n; ++f)
+    if (!tile_map(&maps.m[f], fi.p[f], g.nxh, g.nz, g.ny, p.batch, p.rows_in)) {
+      map_failed(c);
+      return;
+    }
+  const dim3 gz(cdiv(g.nx / 2, p.batch), g.ny, n);
+  if (p.ept == 12 && p.batch == 4)
+    LMVD_LAUNCH(c, KC_FFT_Z_INV, fl, by, (k_fft_z_inv<C, 12, 4, IN_DF>), gz, threads(p), smem_bytes(p), p, g, maps, T,
+                tstride, c.dflags);
+  else if (p.ept == 12)
+    LMVD_LAUNCH(c, KC_FFT_Z_INV, fl, by, (k_fft_z_inv<C, 12, 2, IN_DF>), gz, threads(p), smem_bytes(p), p, g, maps, T,
+                tstride, c.dflags);
+  else
+    LMVD_LAUNCH(c, KC_FFT_Z_INV, fl, by, (k_fft_z_inv<C, 6, 4, IN_DF>), gz, threads(p), smem_bytes(p), p, g, maps, T,
+                tstride, c.dflags);
+}
+
+template <class C>
+static void z_fwd_launch(Ctx& c, const C* T, int n, const FieldsW& fo, double fl, double by) {
+  const Grid& g = c.g;
+  const FFTPlan& p = c.fz;
+  ZMaps maps;
+  if (!tile_map(&maps.m[0], T, g.nx / 2, g.pz, (size_t)n * g.ny, p.batch, p.rows_t)) {
+    map_failed(c);
+    return;
+  }
+  const dim3 gz(cdiv(g.nx / 2 + 1, p.batch), g.ny, n);
+  if (p.ept == 12 && p.batch == 4)
+    LMVD_LAUNCH(c, KC_FFT_Z_FWD, fl, by, (k_fft_z_fwd<C, 12, 4>), gz, threads(p), smem_bytes(p), p, g, maps, fo,
+                c.dflags);
+  else if (p.ept == 12)
+    LMVD_LAUNCH(c, KC_FFT_Z_FWD, fl, by, (k_fft_z_fwd<C, 12, 2>), gz, threads(p), smem_bytes(p), p, g, maps, fo,
+                c.dflags);
+  else
+    LMVD_LAUNCH(c, KC_FFT_Z_FWD, fl, by, (k_fft_z_fwd<C, 6, 4>), gz, threads(p), smem_bytes(p), p, g, maps, fo,
+                c.dflags);
+}
 
 template <class C>
 static void inverse_t(Ctx& c, cd* const* in, void* const* out, int nf, const void* wmul = nullptr, bool in_df = false) {
@@ -641,21 +803,10 @@ static void inverse_t(Ctx& c, cd* const* in, void* const* out, int nf, const voi
       fo.p[f] = out[f0 + f];
     }
     const double h = g.nx / 2, ny = g.ny, pz = g.pz, px = g.px;
-    dim3 gz(cdiv(g.nx / 2, c.fz.batch), g.ny, n);
     const double zfl = n * ny * h * fft_flops(pz), zby = n * ny * h * 16.0 * ((g.nz - 1) + pz);
     // double-float inputs only exist for the double-float arithmetic
-    if (in_df && c.fz.ept == 12)
-      LMVD_LAUNCH(c, KC_FFT_Z_INV, zfl, zby, (k_fft_z_inv<C, 12, std::is_same<C, cdf>::value>), gz, threads(c.fz),
-                  smem_bytes(c.fz), c.fz, g, fi, T, tstride);
-    else if (in_df)
-      LMVD_LAUNCH(c, KC_FFT_Z_INV, zfl, zby, (k_fft_z_inv<C, 6, std::is_same<C, cdf>::value>), gz, threads(c.fz),
-                  smem_bytes(c.fz), c.fz, g, fi, T, tstride);
-    else if (c.fz.ept == 12)
-      LMVD_LAUNCH(c, KC_FFT_Z_INV, zfl, zby, (k_fft_z_inv<C, 12>), gz, threads(c.fz), smem_bytes(c.fz), c.fz, g, fi,
-                  T, tstride);
-    else
-      LMVD_LAUNCH(c, KC_FFT_Z_INV, zfl, zby, (k_fft_z_inv<C, 6>), gz, threads(c.fz), smem_bytes(c.fz), c.fz, g, fi,
-                  T, tstride);
+    if (in_df && std::is_same<C, cdf>::value) z_inv_launch<C, std::is_same<C, cdf>::value>(c, fi, n, T, tstride, zfl, zby);
+    else z_inv_launch<C, false>(c, fi, n, T, tstride, zfl, zby);
     dim3 gx(cdiv(cdiv(g.pz, 2), c.fx.batch), g.ny, n);
     const double xfl = n * ny * ((g.pz + 1) / 2) * fft_flops(px), xby = n * ny * pz * (16.0 * h + 8.0 * px);
     if (wmul) {  // the product with w in the epilogue: one more physical field read, one multiply per point
@@ -696,13 +847,7 @@ static void forward_t(Ctx& c, void* const* in, cd* const* out, int nf) {
     else
       LMVD_LAUNCH(c, KC_FFT_X_FWD, n * ny * ((g.pz + 1) / 2) * fft_flops(px), n * ny * pz * (16.0 * h + 8.0 * px),
                   (k_fft_x_fwd<C, 6>), gx, threads(c.fx), smem_bytes(c.fx), c.fx, g, fi, T, tstride);
-    dim3 gz(cdiv(g.nx / 2 + 1, c.fz.batch), g.ny, n);
-    if (c.fz.ept == 12)
-      LMVD_LAUNCH(c, KC_FFT_Z_FWD, n * ny * h * fft_flops(pz), n * ny * 16.0 * (pz * h + (double)g.nz * g.nxh),
-                  (k_fft_z_fwd<C, 12>), gz, threads(c.fz), smem_bytes(c.fz), c.fz, g, T, tstride, fo);
-    else
-      LMVD_LAUNCH(c, KC_FFT_Z_FWD, n * ny * h * fft_flops(pz), n * ny * 16.0 * (pz * h + (double)g.nz * g.nxh),
-                  (k_fft_z_fwd<C, 6>), gz, threads(c.fz), smem_bytes(c.fz), c.fz, g, T, tstride, fo);
+    z_fwd_launch<C>(c, T, n, fo, n * ny * h * fft_flops(pz), n * ny * 16.0 * (pz * h + (double)g.nz * g.nxh));
   }
 }
 
@@ -728,13 +873,7 @@ static void forward_dot3_t(Ctx& c, const double* const* w, const double* const* 
   else
     LMVD_LAUNCH(c, KC_FFT_X_FWD, xfl, xby, (k_fft_x_fwd_dot3<C, 6>), gx, threads(c.fx), smem_bytes(c.fx), c.fx, g, T,
                 tstride, d);
-  dim3 gz(cdiv(g.nx / 2 + 1, c.fz.batch), g.ny, 1);
-  if (c.fz.ept == 12)
-    LMVD_LAUNCH(c, KC_FFT_Z_FWD, ny * h * fft_flops(pz), ny * 16.0 * (pz * h + (double)g.nz * g.nxh),
-                (k_fft_z_fwd<C, 12>), gz, threads(c.fz), smem_bytes(c.fz), c.fz, g, T, tstride, fo);
-  else
-    LMVD_LAUNCH(c, KC_FFT_Z_FWD, ny * h * fft_flops(pz), ny * 16.0 * (pz * h + (double)g.nz * g.nxh),
-                (k_fft_z_fwd<C, 6>), gz, threads(c.fz), smem_bytes(c.fz), c.fz, g, T, tstride, fo);
+  z_fwd_launch<C>(c, T, 1, fo, ny * h * fft_flops(pz), ny * 16.0 * (pz * h + (double)g.nz * g.nxh));
 }
 
 void fft_inverse_mul(Ctx& c, cd* in, double* out, const double* w) {
@@ -813,10 +952,7 @@ int noalloc_setup(int dev, void** ptr) {
   }
   void* p = nullptr;
   if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return LMVD_ERR_CUDA;
-  if (cudaFuncSetAttribute(k_fft_z_inv<cd, 12>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess ||
-      cudaFuncSetAttribute(k_fft_x_inv<cd, 12>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess ||
-      cudaFuncSetAttribute(k_fft_z_inv<cd, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess ||
-      cudaFuncSetAttribute(k_fft_x_inv<cd, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess)
+  if (set_smem<cd>())
     return LMVD_ERR_CUDA;
   g_noalloc_ptr[dev] = p;
   *ptr = p;
@@ -847,7 +983,7 @@ extern "C" int lmvd_inverse_transform_noalloc(int nx, int ny, int nz, const void
   FFTPlan fx, fz;
   if (!make_plan(g.px, FFT_CTA_X, fx) || !make_plan(g.pz, FFT_CTA_Z, fz)) return LMVD_ERR_UNSUPPORTED;
   for (FFTPlan* p : {&fx, &fz})
-    if (smem_bytes(*p) > 200 * 1024) return LMVD_ERR_UNSUPPORTED;
+    if (smem_bytes(*p) > kFftSmemMax) return LMVD_ERR_UNSUPPORTED;
   // scratch layout: x twiddles | z twiddles | one field's intermediate T[ny][pz][nx/2]
   const size_t off_tz = align256(sizeof(double2) * g.px);
   const size_t off_tb = off_tz + align256(sizeof(double2) * g.pz);
@@ -875,9 +1011,12 @@ extern "C" int lmvd_inverse_transform_noalloc(int nx, int ny, int nz, const void
     FieldsRW fo{};
     fi.p[0] = (const cd*)spec + (size_t)f * S;
     fo.p[0] = phys + (size_t)f * P;
+    ZMaps maps;
+    if (!tile_map(&maps.m[0], fi.p[0], g.nxh, nz, ny, fz.batch, fz.rows_in)) return LMVD_ERR_CUDA;
     dim3 gz(cdiv(nx / 2, fz.batch), ny, 1);
-    if (fz.ept == 12) k_fft_z_inv<cd, 12><<<gz, threads(fz), smem_bytes(fz), st>>>(fz, g, fi, T, 0);
-    else k_fft_z_inv<cd, 6><<<gz, threads(fz), smem_bytes(fz), st>>>(fz, g, fi, T, 0);
+    if (fz.ept == 12 && fz.batch == 4) k_fft_z_inv<cd, 12, 4><<<gz, threads(fz), smem_bytes(fz), st>>>(fz, g, maps, T, 0, nullptr);
+    else if (fz.ept == 12) k_fft_z_inv<cd, 12, 2><<<gz, threads(fz), smem_bytes(fz), st>>>(fz, g, maps, T, 0, nullptr);
+    else k_fft_z_inv<cd, 6, 4><<<gz, threads(fz), smem_bytes(fz), st>>>(fz, g, maps, T, 0, nullptr);
     if (cudaGetLastError() != cudaSuccess) return LMVD_ERR_CUDA;
     dim3 gx(cdiv(cdiv(g.pz, 2), fx.batch), ny, 1);
     if (fx.ept == 12) k_fft_x_inv<cd, 12><<<gx, threads(fx), smem_bytes(fx), st>>>(fx, g, T, 0, fo);

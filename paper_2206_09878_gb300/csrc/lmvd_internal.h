@@ -175,7 +175,10 @@ struct FFTPlan {
   int batch = 1;           // transforms per CTA
   int ept = 12;            // elements per thread (a multiple of every radix of the plan)
   int tpt = 1;             // threads per transform = n / ept; a CTA has tpt * batch threads
-  int pad = 1;             // shared-memory leading dimension of a transform: n + pad
+  int pad = 1;             // shared-memory leading dimension of a transform: n + pad (x-passes; the z-passes
+                           // interleave their batch columns, pad 0)
+  int rows_in = 0;         // z-passes: rows per tile copy of the spectral input (divides nz / 2) ...
+  int rows_t = 0;          // ... and of the intermediate T (divides pz); 0 for the x-passes
   double scale_d = 1.0;    // 1 / (2 px pz) for the forward z-pass (with the x-pass's 1/2)
   df scale_f{1.f, 0.f};
   df s3f{0.f, 0.f};        // sin(2 pi / 3) as a double-float
