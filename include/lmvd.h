@@ -275,7 +275,9 @@ int lmvd_substage_index(const lmvd_ctx* ctx);
 /* Block until all work of the context's stream is done; returns the latched status or CUDA.
  * Failure detection: every substage checks its new state on the device (inf or nan anywhere in z,
  * Omega2, m2^d or the means sets a device status word, no host synchronisation); this call reads that
- * word and latches LMVD_ERR_NONFINITE if it is set. */
+ * word and latches LMVD_ERR_NONFINITE if it is set. The z-passes of the transforms wait at most ~1 s for
+ * their tile copies (TMA); a copy that did not complete sets another bit of the word, which this call
+ * latches as LMVD_ERR_CUDA (the results of that transform are not valid). */
 int lmvd_synchronize(lmvd_ctx* ctx);
 
 /* First error latched in the context (LMVD_OK if none; a non-finite state is latched by the next
@@ -335,6 +337,15 @@ const char* lmvd_strerror(int code);
  * second (CUDA-event time) to *ops_per_second. Synchronous; allocates and frees a small output array.
  * Errors: INVALID_ARG (NULL output, iters < 1, op outside 0..3), OOM, CUDA. */
 int lmvd_rate_probe(int op, int iters, double* ops_per_second, void* cuda_stream);
+
+/* The bounded wait of the transforms' tile copies, on its own (no paper counterpart: it tests the failure
+ * path of lmvd_synchronize's tile-copy bit without a fault). One CTA copies 128 bytes from src (device,
+ * 16-byte aligned, at least 16 doubles) into shared memory while its mbarrier expects 128 + extra_bytes;
+ * extra_bytes = 0 completes (and the copy is checked: bit 3 of *status if it differs), extra_bytes > 0
+ * (a multiple of 16, at most 1024) never completes, and the CTA gives up after ~1 s of SM clock and sets
+ * bit 2 of *status (device word, caller-owned, not cleared). Asynchronous on cuda_stream (NULL = legacy
+ * default stream). Errors: INVALID_ARG (NULL or unaligned pointer, extra_bytes out of range), CUDA. */
+int lmvd_tile_wait_probe(const double* src, int extra_bytes, unsigned* status, void* cuda_stream);
 
 /* 1 if this library was built with the kernels' index checks (-DLMVD_CHECK, liblmvd_check.so), else 0
  * (no paper counterpart: the checked build is a testing aid). In the checked build every checked access

@@ -1105,6 +1105,7 @@ int lmvd_synchronize(lmvd_ctx* h) {
     return latch(c, LMVD_ERR_CUDA);
   if (flags & 1u) latch(c, LMVD_ERR_NONFINITE);
   if (flags & 2u) latch(c, LMVD_ERR_FP_DIVERGED);
+  if (flags & 4u) latch(c, LMVD_ERR_CUDA);  // a z-pass tile copy did not complete within its time limit
   if (kCheckedBuild && (oob_take_api() | oob_take_fft() | oob_take_yk() | oob_take_pw() | oob_take_adj()))
     latch(c, LMVD_ERR_OUT_OF_BOUNDS);
   return c.status;

@@ -301,6 +301,13 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
+// bytes (a multiple of 16, both addresses 16-byte aligned) from src to dst; completes them on bar
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+
 // Every thread waits for phase 0 of bar, for at most ~1 s of SM clock; false (and bit 2 of the context's
 // status word, when there is one) if the copies did not complete by then.
 __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned* flags) {
@@ -888,6 +895,21 @@ void fft_forward_dot3(Ctx& c, const double* const* w, const double* const* m, cd
   else forward_dot3_t<cd>(c, w, m, out);
 }
 
+// The bounded wait of the z-passes, on its own (lmvd_tile_wait_probe): one CTA expects 128 + extra bytes on
+// an mbarrier and copies 128 of them; with extra > 0 the phase never completes and the wait gives up.
+__global__ void k_tile_wait_probe(const double* src, int extra, unsigned* status) {
+  __shared__ __align__(128) double buf[16];
+  __shared__ __align__(8) unsigned long long bar;
+  if (threadIdx.x == 0) mbar_init(&bar);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    mbar_expect_tx(&bar, 128u + (unsigned)extra);
+    bulk_load(buf, src, 128u, &bar);
+  }
+  if (!mbar_wait_bounded(&bar, status)) return;
+  if (threadIdx.x < 16 && buf[threadIdx.x] != src[threadIdx.x]) atomicOr(status, 8u);
+}
+
 void fft_inverse_as(Ctx& c, cd* const* in, double* const* out, int nf, int precision) {
   void* o[64];
   for (int f = 0; f < nf; ++f) o[f] = out[f];
@@ -1024,4 +1046,13 @@ extern "C" int lmvd_inverse_transform_noalloc(int nx, int ny, int nz, const void
     if (cudaGetLastError() != cudaSuccess) return LMVD_ERR_CUDA;
   }
   return LMVD_OK;
+}
+
+extern "C" int lmvd_tile_wait_probe(const double* src, int extra_bytes, unsigned* status, void* cuda_stream) {
+  using namespace lmvd;
+  if (!src || !status || ((uintptr_t)src & 15) || extra_bytes < 0 || extra_bytes > 1024 || (extra_bytes & 15))
+    return LMVD_ERR_INVALID_ARG;
+  (void)cudaGetLastError();
+  k_tile_wait_probe<<<1, 32, 0, (cudaStream_t)cuda_stream>>>(src, extra_bytes, status);
+  return cudaGetLastError() == cudaSuccess ? LMVD_OK : LMVD_ERR_CUDA;
 }

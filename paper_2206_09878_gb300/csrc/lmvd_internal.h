@@ -268,7 +268,8 @@ struct Ctx {
   Prof prof;
   AdjWork* adj = nullptr;
   unsigned* dflags = nullptr;  // device status word: bit 0 = a non-finite value in the state (k_check_finite),
-                               // bit 1 = the fixed point did not converge (diagnostics on)
+                               // bit 1 = the fixed point did not converge (diagnostics on), bit 2 = a z-pass
+                               // tile copy (TMA) did not complete within its ~1 s wait (the CTA skipped its work)
   // diagnostics record of the last substage (lmvd_diagnostics): [0, 1] = |mass residual|^2, |rho_t|^2,
   // [2 + 2k, 3 + 2k] = |dz/dt^{k+1} - dz/dt^k|^2, |dz/dt^{k+1}|^2 for k < kf; [DIAG_KE] = kinetic energy,
   // [DIAG_MMAX] = max |m|^2 over the grid (the bits of a non-negative double, ordered as an integer),

@@ -79,6 +79,7 @@ def _load():
         "lmvd_df64_convert": (I, [P, P, P, P, P, P, S, P]),
         "lmvd_checked_build": (I, []),
         "lmvd_rate_probe": (I, [I, I, ctypes.POINTER(ctypes.c_double), P]),
+        "lmvd_tile_wait_probe": (I, [P, I, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -97,7 +98,7 @@ EXPORTED = ("lmvd_default_config", "lmvd_create", "lmvd_destroy", "lmvd_set_stat
             "lmvd_forward_transform", "lmvd_inverse_transform_noalloc", "lmvd_state_bytes",
             "lmvd_adjoint_substage", "lmvd_adjoint_startup", "lmvd_device_bytes", "lmvd_diagnostics_enable",
             "lmvd_diagnostics", "lmvd_graphs_enable", "lmvd_graph_count", "lmvd_df64_convert",
-            "lmvd_checked_build", "lmvd_rate_probe")
+            "lmvd_checked_build", "lmvd_rate_probe", "lmvd_tile_wait_probe")
 LMVD_KERNEL_CLASSES = 13
 
 
@@ -231,6 +232,13 @@ def lmvd_rate_probe(op, iters=20000, stream=None):
     st = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
     _check(_lib.lmvd_rate_probe(int(op), int(iters), ctypes.byref(out), st), "lmvd_rate_probe")
     return out.value
+
+
+def lmvd_tile_wait_probe(src, extra_bytes, status, stream=None):
+    """The transforms' bounded tile-copy wait on its own: src a CUDA float64 tensor (>= 16 values), status a
+    CUDA int32 tensor of one element (bit 2: the wait gave up; bit 3: the copied data differ)."""
+    st = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
+    _check(_lib.lmvd_tile_wait_probe(_ptr(src), int(extra_bytes), _ptr(status), st), "lmvd_tile_wait_probe")
 
 
 def lmvd_state_bytes(h):

@@ -112,6 +112,11 @@ def test_host_side_argument_checks_without_gpu(lib):
     assert L.lmvd_rate_probe(0, 10, None, None) == -1                                  # NULL output
     assert L.lmvd_rate_probe(4, 10, ctypes.byref(out), None) == -1                     # unknown op
     assert L.lmvd_rate_probe(0, 0, ctypes.byref(out), None) == -1                      # no iterations
+    assert L.lmvd_tile_wait_probe(None, 0, fake, None) == -1                          # NULL source
+    assert L.lmvd_tile_wait_probe(ctypes.c_void_p(24), 0, fake, None) == -1           # source not 16-byte aligned
+    assert L.lmvd_tile_wait_probe(fake, 8, fake, None) == -1                          # extra not a multiple of 16
+    assert L.lmvd_tile_wait_probe(fake, 2048, fake, None) == -1                       # extra beyond 1024
+    assert L.lmvd_tile_wait_probe(fake, 16, None, None) == -1                         # NULL status
     assert L.lmvd_df64_convert(None, None, None, None, None, None, 0, None) == 0      # nothing to do
     assert L.lmvd_df64_convert(None, None, None, None, None, None, 4, None) == -1
 

@@ -11,6 +11,9 @@
 * At density ratio 100 with a sharp interface the fixed point does not converge (the oracle shows
   relative changes above 1 throughout); lmvd_synchronize returns LMVD_ERR_FP_DIVERGED. At the paper's
   density ratios it stays clean.
+* The transforms' tile copies wait on an mbarrier with a time limit: a copy that cannot complete (more
+  bytes expected than sent, through lmvd_tile_wait_probe) makes the CTA give up after ~1 s and set the
+  status bit that lmvd_synchronize reports as LMVD_ERR_CUDA, with no fault and the device still usable.
 """
 import numpy as np
 import pytest
@@ -154,6 +157,32 @@ def test_oversized_grid_reports_oom_and_the_device_stays_usable(L):
     assert L._lib.lmvd_create(ctypes.byref(cfg), None, ctypes.byref(h)) == -3     # LMVD_ERR_OOM
     assert not h.value
     S, ctx, st, _ = make_pair(L, "rt32")
+    ctx.set_state(to_torch(st))
+    ctx.advance_substage()
+    assert L._lib.lmvd_synchronize(ctx.h) == 0
+    ctx.close()
+
+
+def test_tile_copy_wait_gives_up_and_is_reported(L):
+    """The transforms' tile copies complete on an mbarrier that every thread waits for with a time limit
+    (~1 s of SM clock). lmvd_tile_wait_probe runs that wait alone: with the expected bytes delivered it
+    completes at once and the data arrive; with 16 bytes more expected than copied it can never complete,
+    the CTA gives up after the limit and sets bit 2 of the status word (the bit lmvd_synchronize turns into
+    LMVD_ERR_CUDA), and the device stays usable."""
+    import time
+    src = torch.arange(16, dtype=torch.float64, device="cuda")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    L.lmvd_tile_wait_probe(src, 0, status)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    t0 = time.time()
+    L.lmvd_tile_wait_probe(src, 16, status)
+    torch.cuda.synchronize()
+    waited = time.time() - t0
+    assert int(status.item()) == 4
+    assert 0.2 < waited < 30
+    from _pairs import make_pair, to_torch
+    S, ctx, st, cfg = make_pair(L, "rt32")
     ctx.set_state(to_torch(st))
     ctx.advance_substage()
     assert L._lib.lmvd_synchronize(ctx.h) == 0
