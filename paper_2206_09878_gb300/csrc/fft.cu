@@ -370,6 +370,21 @@ __global__ void __launch_bounds__(FFT_CTA_Z, FftMinCtas<C>::z_inv)
   }
 }
 
+// (row, column) of a flat index idx = row n + column that a thread advances by a fixed step: one division at
+// the start instead of one per element (n is a run-time value, and an integer division costs tens of
+// instructions in passes that are bound by their instruction issue).
+struct RowCol {
+  int r, c;
+  __device__ __forceinline__ RowCol(int idx, int n) : r(idx / n), c(idx - (idx / n) * n) {}
+  __device__ __forceinline__ void advance(int step, int n) {
+    c += step;
+    while (c >= n) {
+      c -= n;
+      ++r;
+    }
+  }
+};
+
 // ---------------------------------------------------------------- inverse x-pass (c2r, 2 rows per transform)
 // With MUL the epilogue stores w * phys instead of phys (w: a physical field of the same layout, one for all
 // fields of the launch): the product f'(z) dz/dt of the fixed point (Sec. 4.3) formed as the transform is
@@ -387,15 +402,17 @@ __device__ __forceinline__ void x_inv_body(const FFTPlan& pl, const Grid& g, con
   for (int idx = threadIdx.x; idx < batch * ld; idx += blockDim.x) a[idx] = F::zero();
   __syncthreads();
   const C* src = T + f * tstride + (size_t)j * pz * h;
+  RowCol rc(threadIdx.x, h);
   for (int base = threadIdx.x; base < batch * h; base += FFT_LOAD_CHUNK * blockDim.x) {
     C ta[FFT_LOAD_CHUNK], tb[FFT_LOAD_CHUNK];
     int kk[FFT_LOAD_CHUNK], bs[FFT_LOAD_CHUNK];
 #pragma unroll
     for (int u = 0; u < FFT_LOAD_CHUNK; ++u) {
       const int idx = base + u * blockDim.x;
+      const int bb = rc.r, k = rc.c;
+      rc.advance(blockDim.x, h);
       kk[u] = -1;
       if (idx >= batch * h) continue;
-      const int bb = idx / h, k = idx - bb * h;
       const int za = 2 * (pr0 + bb), zb = za + 1;
       if (za >= pz) continue;
       if (!LMVD_IN((size_t)za * h + k, (size_t)pz * h) || !LMVD_IN(bb * ld + px - 1, batch * ld)) continue;
@@ -423,15 +440,17 @@ __device__ __forceinline__ void x_inv_body(const FFTPlan& pl, const Grid& g, con
   R* dst = reinterpret_cast<R*>(pick(out.p, f)) + (size_t)j * g.P;
   if (MUL) {
     const R* w = reinterpret_cast<const R*>(wmul) + (size_t)j * g.P;
+    RowCol rw(threadIdx.x, px);
     for (int base = threadIdx.x; base < batch * px; base += FFT_LOAD_CHUNK * blockDim.x) {
       R wa[FFT_LOAD_CHUNK], wb[FFT_LOAD_CHUNK];
       int xs[FFT_LOAD_CHUNK], bs[FFT_LOAD_CHUNK];
 #pragma unroll
       for (int u = 0; u < FFT_LOAD_CHUNK; ++u) {
         const int idx = base + u * blockDim.x;
+        const int bb = rw.r, x = rw.c;
+        rw.advance(blockDim.x, px);
         xs[u] = -1;
         if (idx >= batch * px) continue;
-        const int bb = idx / px, x = idx - bb * px;
         const int za = 2 * (pr0 + bb), zb = za + 1;
         if (za >= pz) continue;
         if (!LMVD_IN((size_t)za * px + x, g.P) || !LMVD_IN(bb * ld + x, batch * ld)) continue;
@@ -451,8 +470,10 @@ __device__ __forceinline__ void x_inv_body(const FFTPlan& pl, const Grid& g, con
     }
     return;
   }
+  RowCol ro(threadIdx.x, px);
   for (int idx = threadIdx.x; idx < batch * px; idx += blockDim.x) {
-    const int bb = idx / px, x = idx - bb * px;
+    const int bb = ro.r, x = ro.c;
+    ro.advance(blockDim.x, px);
     const int za = 2 * (pr0 + bb), zb = za + 1;
     if (za >= pz) continue;
     if (!LMVD_IN((size_t)za * px + x, g.P) || !LMVD_IN(bb * ld + x, batch * ld)) continue;
@@ -492,16 +513,18 @@ __device__ __forceinline__ void x_fwd_body(const FFTPlan& pl, const Grid& g, con
   const R* src = reinterpret_cast<const R*>(pick(in.p, f)) + (size_t)j * g.P;
   // DOT3 reads six fields per point: fewer points per chunk keep the registers in check
   constexpr int CH = DOT3 ? 2 : FFT_LOAD_CHUNK;
+  RowCol rc(threadIdx.x, px);
   for (int base = threadIdx.x; base < batch * px; base += CH * blockDim.x) {
     R va[CH], vb[CH];
     int ds[CH];
 #pragma unroll
     for (int u = 0; u < CH; ++u) {
       const int idx = base + u * blockDim.x;
+      const int bb = rc.r, x = rc.c;
+      rc.advance(blockDim.x, px);
       ds[u] = -1;
       va[u] = vb[u] = F::rzero();
       if (idx >= batch * px) continue;
-      const int bb = idx / px, x = idx - bb * px;
       const int za = 2 * (pr0 + bb), zb = za + 1;
       if (!LMVD_IN(bb * ld + x, batch * ld)) continue;
       ds[u] = bb * ld + x;
@@ -534,8 +557,10 @@ __device__ __forceinline__ void x_fwd_body(const FFTPlan& pl, const Grid& g, con
   fft_inplace<C, -1, EPT, false, kPrune<C>>(a + bt * ld, pl, tt, pl.tpt, h, px - h + 1);  // truncated kx
   const C* res = a;
   C* dst = T + f * tstride + (size_t)j * pz * h;
+  RowCol ro(threadIdx.x, h);
   for (int idx = threadIdx.x; idx < batch * h; idx += blockDim.x) {
-    const int bb = idx / h, k = idx - bb * h;
+    const int bb = ro.r, k = ro.c;
+    ro.advance(blockDim.x, h);
     const int za = 2 * (pr0 + bb), zb = za + 1;
     if (za >= pz) continue;
     if (!LMVD_IN((size_t)za * h + k, (size_t)pz * h) || !LMVD_IN(bb * ld + px - 1, batch * ld)) continue;
