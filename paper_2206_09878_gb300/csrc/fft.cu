@@ -13,7 +13,9 @@
 //            with every rounding of the pass).
 // Synthesis is unnormalised: f(x, z) = sum_k fhat_k exp(i (k1 x + k3 z)).
 // A pass is one CTA per (plane, field, batch of columns / row pairs); every 1D transform is a
-// Stockham autosort FFT in shared memory with radix-4/3/2 stages and a precomputed twiddle table.
+// Stockham autosort FFT in shared memory with radix-4/3/2 stages and a precomputed twiddle table. The
+// x-passes read and write their contiguous rows with the CTA's threads; the z-passes fetch their columns
+// with TMA tile copies (cp.async.bulk.tensor) and write them with the threads.
 //
 // Arithmetic: complex double (precision 0) or complex double-float (precision 1, df64.h) selected
 // by the complex type C. Spectral inputs and outputs are always complex double; the intermediate
@@ -244,7 +246,8 @@ constexpr bool kPrune = std::is_same<C, cd>::value;
 // and fit fewer CTAs, whose warps hide less of the FP64 pipe's latency. The x-passes run small CTAs (2
 // transforms of 768 points, 6-7 per SM), so that the load, compute and store phases of different CTAs
 // (separated by barriers) overlap: 7-8% faster in double-float at 512^3 than 256-thread CTAs. The z-passes
-// gather `batch` kx columns of each z-row, so they keep 4 of them per CTA (64-byte row segments).
+// take 4 kx columns per CTA (2 when 4 transforms do not fit FFT_CTA_Z threads); with 2 at 768 points the
+// double-float inverse z-pass was 13% slower.
 constexpr int FFT_CTA_X = 128, FFT_CTA_Z = 256;
 // CTAs per SM each pass is compiled for, i.e. its register cap. FP64: 6 x-pass and 3 z-pass CTAs (80
 // registers). Double-float: the x-passes fit 7 CTAs at 72 registers without spilling (inverse 1.5%, forward
@@ -258,8 +261,9 @@ template <>
 struct FftMinCtas<cdf> {
   static constexpr int x = 7, z_inv = 3, z_fwd = 4;
 };
-// Loads a thread issues in its gather / scatter loops before it stores any of them: one load at a time would
-// serialise a memory latency per iteration (ncu: long-scoreboard stalls dominated the double-float passes).
+// Loads a thread issues in the x-passes' gather loops before it stores any of them: one load at a time
+// would serialise a memory latency per iteration (ncu: long-scoreboard stalls dominated the double-float
+// passes). The z-passes fetch their tiles with TMA instead (below).
 constexpr int FFT_LOAD_CHUNK = 4;
 
 // ---------------------------------------------------------------- tile loads (TMA)
