@@ -242,6 +242,13 @@ __device__ void fft_inplace(C* x, const FFTPlan& pl, int tt, int tpt, int lo = 0
 template <class C>
 constexpr bool kPrune = std::is_same<C, cd>::value;
 
+// Whether fft_inplace with PZ = kPrune<C> skips a zero input band of plan pl: only a first radix-4 stage
+// prunes, so a plan without one (n with a single factor 2) reads the band and it must hold zeros.
+template <class C>
+__device__ __forceinline__ bool prunes_zero_band(const FFTPlan& pl) {
+  return kPrune<C> && (pl.code & 3u) == 0 && pl.nst > 1;
+}
+
 // Launch bounds: every pass caps its registers (FftMinCtas below); the FP64 kernels would otherwise take ~100
 // and fit fewer CTAs, whose warps hide less of the FP64 pipe's latency. The x-passes run small CTAs (2
 // transforms of 768 points, 6-7 per SM), so that the load, compute and store phases of different CTAs
@@ -354,12 +361,13 @@ __global__ void __launch_bounds__(FFT_CTA_Z, FftMinCtas<C>::z_inv)
   }
   if (!mbar_wait_bounded(bar, flags)) return;
   constexpr bool convert = !IN_DF && !std::is_same<C, cd>::value;
-  if constexpr (!kPrune<C> || convert) {
+  const bool zero_band = !prunes_zero_band<C>(pl);
+  if (zero_band || convert) {
     // the padding band [n2, pz - n2 + 1) zeroed where the arithmetic reads it; spectral doubles to pairs
     for (int idx = threadIdx.x; idx < pz * COLS; idx += blockDim.x) {
       const int z = idx / COLS;
       if (z >= n2 && z < pz - n2 + 1) {
-        if (!kPrune<C>) a[idx] = F::zero();
+        if (zero_band) a[idx] = F::zero();
       } else if (convert) {
         a[idx] = F::from_spec(reinterpret_cast<const cd*>(a)[idx]);
       }
@@ -395,7 +403,7 @@ struct RowCol {
 // written, so neither dz/dt on the grid nor a separate product pass is needed.
 template <class C, int EPT, bool MUL>
 __device__ __forceinline__ void x_inv_body(const FFTPlan& pl, const Grid& g, const C* T, size_t tstride,
-                                           const FieldsRW& out, const void* wmul) {
+                                           const FieldsRW& out, const void* wmul, unsigned* flags) {
   using F = FT<C>;
   using R = typename F::R;
   extern __shared__ __align__(128) unsigned char sm_raw[];
@@ -403,39 +411,61 @@ __device__ __forceinline__ void x_inv_body(const FFTPlan& pl, const Grid& g, con
   const int batch = pl.batch, ld = pl.n + pl.pad, px = g.px, pz = g.pz, h = g.nx / 2;
   const int pr0 = blockIdx.x * batch, j = blockIdx.y, f = blockIdx.z;
   const int bt = threadIdx.x / pl.tpt, tt = threadIdx.x - bt * pl.tpt;
-  for (int idx = threadIdx.x; idx < batch * ld; idx += blockDim.x) a[idx] = F::zero();
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(sm_raw + (size_t)batch * ld * sizeof(C));
+  if (threadIdx.x == 0) mbar_init(bar);
   __syncthreads();
-  const C* src = T + f * tstride + (size_t)j * pz * h;
-  RowCol rc(threadIdx.x, h);
-  for (int base = threadIdx.x; base < batch * h; base += FFT_LOAD_CHUNK * blockDim.x) {
-    C ta[FFT_LOAD_CHUNK], tb[FFT_LOAD_CHUNK];
-    int kk[FFT_LOAD_CHUNK], bs[FFT_LOAD_CHUNK];
-#pragma unroll
-    for (int u = 0; u < FFT_LOAD_CHUNK; ++u) {
-      const int idx = base + u * blockDim.x;
-      const int bb = rc.r, k = rc.c;
-      rc.advance(blockDim.x, h);
-      kk[u] = -1;
-      if (idx >= batch * h) continue;
-      const int za = 2 * (pr0 + bb), zb = za + 1;
-      if (za >= pz) continue;
-      if (!LMVD_IN((size_t)za * h + k, (size_t)pz * h) || !LMVD_IN(bb * ld + px - 1, batch * ld)) continue;
-      kk[u] = k;
-      bs[u] = bb;
-      ta[u] = src[(size_t)za * h + k];
-      tb[u] = zb < pz ? src[(size_t)zb * h + k] : F::zero();
+  // A transform's rows za = 2 (pr0 + bb) and za + 1 of T are contiguous (2 h elements): one bulk copy each
+  // (TMA, cp.async.bulk) into the upper part [h, 3 h) = [h, px) of its buffer, completing on the mbarrier
+  if (threadIdx.x == 0) {
+    const C* src = T + f * tstride + (size_t)j * pz * h;
+    int nb = 0;
+    while (nb < batch && 2 * (pr0 + nb) < pz) ++nb;
+    mbar_expect_tx(bar, (unsigned)(nb * 2 * h * sizeof(C)));
+    for (int bb = 0; bb < nb; ++bb) {
+      const int za = 2 * (pr0 + bb);
+      if (LMVD_IN(bb * ld + px - 1, batch * ld) && LMVD_IN((size_t)(za + 2) * h - 1, (size_t)pz * h))
+        bulk_load(a + bb * ld + h, src + (size_t)za * h, (unsigned)(2 * h * sizeof(C)), bar);
     }
+  }
+  if (!mbar_wait_bounded(bar, flags)) return;
+  // two real rows into one complex transform: y[k] = Xa[k] + i Xb[k], y[px - k] = conj(Xa[k]) + i conj(Xb[k]).
+  // Every thread reads its EPT / 3 pairs (batch h = blockDim.x EPT / 3 of them) before any is written,
+  // since the written y[px - k] overlay the copied rows.
+  constexpr int NP = EPT / 3;
+  C ta[NP], tb[NP];
+  int kk[NP], bs[NP];
+  RowCol rc(threadIdx.x, h);
 #pragma unroll
-    for (int u = 0; u < FFT_LOAD_CHUNK; ++u) {
-      if (kk[u] < 0) continue;
-      const int k = kk[u];
-      C* y = a + bs[u] * ld;
-      if (k == 0) {
-        y[0] = F::make(F::re(ta[u]), F::re(tb[u]));  // the kx = 0 coefficient of a real row is real
-      } else {
-        y[k] = F::add(ta[u], F::ti(tb[u]));                        // Xa[k] + i Xb[k]
-        y[px - k] = F::add(F::cj(ta[u]), F::ti(F::cj(tb[u])));  // conj(Xa[k]) + i conj(Xb[k])
-      }
+  for (int u = 0; u < NP; ++u) {
+    const int bb = rc.r, k = rc.c;
+    rc.advance(blockDim.x, h);
+    kk[u] = -1;
+    if (bb >= batch || 2 * (pr0 + bb) >= pz || !LMVD_IN(bb * ld + 3 * h - 1, batch * ld)) continue;
+    kk[u] = k;
+    bs[u] = bb;
+    ta[u] = a[bb * ld + h + k];
+    tb[u] = a[bb * ld + 2 * h + k];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int u = 0; u < NP; ++u) {
+    if (kk[u] < 0) continue;
+    const int k = kk[u];
+    C* y = a + bs[u] * ld;
+    if (k == 0) {
+      y[0] = F::make(F::re(ta[u]), F::re(tb[u]));  // the kx = 0 coefficient of a real row is real
+    } else {
+      y[k] = F::add(ta[u], F::ti(tb[u]));                        // Xa[k] + i Xb[k]
+      y[px - k] = F::add(F::cj(ta[u]), F::ti(F::cj(tb[u])));  // conj(Xa[k]) + i conj(Xb[k])
+    }
+  }
+  // the padding band [h, px - h + 1) = [h, 2 h]: zero where the arithmetic reads it (it held copied rows)
+  if (!prunes_zero_band<C>(pl)) {
+    RowCol rz(threadIdx.x, h + 1);
+    for (int idx = threadIdx.x; idx < batch * (h + 1); idx += blockDim.x) {
+      const int bb = rz.r, q = rz.c;
+      rz.advance(blockDim.x, h + 1);
+      if (LMVD_IN(bb * ld + h + q, batch * ld)) a[bb * ld + h + q] = F::zero();
     }
   }
   __syncthreads();
@@ -487,13 +517,14 @@ __device__ __forceinline__ void x_inv_body(const FFTPlan& pl, const Grid& g, con
   }
 }
 template <class C, int EPT>
-__global__ void __launch_bounds__(FFT_CTA_X, FftMinCtas<C>::x) k_fft_x_inv(FFTPlan pl, Grid g, const C* T, size_t tstride, FieldsRW out) {
-  x_inv_body<C, EPT, false>(pl, g, T, tstride, out, nullptr);
+__global__ void __launch_bounds__(FFT_CTA_X, FftMinCtas<C>::x) k_fft_x_inv(FFTPlan pl, Grid g, const C* T, size_t tstride, FieldsRW out,
+                                                                         unsigned* flags) {
+  x_inv_body<C, EPT, false>(pl, g, T, tstride, out, nullptr, flags);
 }
 template <class C, int EPT>
 __global__ void __launch_bounds__(FFT_CTA_X, FftMinCtas<C>::x) k_fft_x_inv_mul(FFTPlan pl, Grid g, const C* T, size_t tstride, FieldsRW out,
-                                                                             const void* wmul) {
-  x_inv_body<C, EPT, true>(pl, g, T, tstride, out, wmul);
+                                                                             const void* wmul, unsigned* flags) {
+  x_inv_body<C, EPT, true>(pl, g, T, tstride, out, wmul, flags);
 }
 
 // ---------------------------------------------------------------- forward x-pass (r2c, 2 rows per transform)
@@ -658,8 +689,8 @@ static bool make_plan(int n, int cta, FFTPlan& p) {
   return true;
 }
 
-// the z-passes' buffer is followed by their mbarrier
-static size_t smem_bytes(const FFTPlan& p) { return (size_t)p.batch * (p.n + p.pad) * sizeof(cd) + (p.rows_t ? 16 : 0); }
+// a pass's buffer is followed by its mbarrier (the z-passes' and the inverse x-pass's copies)
+static size_t smem_bytes(const FFTPlan& p) { return (size_t)p.batch * (p.n + p.pad) * sizeof(cd) + 16; }
 
 // Tensor maps for the z-passes' tile copies. cuTensorMapEncodeTiled is a driver function; the runtime hands
 // out its address, so the library needs no link to the driver library.
@@ -848,16 +879,16 @@ static void inverse_t(Ctx& c, cd* const* in, void* const* out, int nf, const voi
     if (wmul) {  // the product with w in the epilogue: one more physical field read, one multiply per point
       if (c.fx.ept == 12)
         LMVD_LAUNCH(c, KC_FFT_X_INV, xfl + n * ny * pz * px, xby + n * ny * pz * 8.0 * px, (k_fft_x_inv_mul<C, 12>),
-                    gx, threads(c.fx), smem_bytes(c.fx), c.fx, g, T, tstride, fo, wmul);
+                    gx, threads(c.fx), smem_bytes(c.fx), c.fx, g, T, tstride, fo, wmul, c.dflags);
       else
         LMVD_LAUNCH(c, KC_FFT_X_INV, xfl + n * ny * pz * px, xby + n * ny * pz * 8.0 * px, (k_fft_x_inv_mul<C, 6>),
-                    gx, threads(c.fx), smem_bytes(c.fx), c.fx, g, T, tstride, fo, wmul);
+                    gx, threads(c.fx), smem_bytes(c.fx), c.fx, g, T, tstride, fo, wmul, c.dflags);
     } else if (c.fx.ept == 12) {
       LMVD_LAUNCH(c, KC_FFT_X_INV, xfl, xby, (k_fft_x_inv<C, 12>), gx, threads(c.fx), smem_bytes(c.fx), c.fx, g, T,
-                  tstride, fo);
+                  tstride, fo, c.dflags);
     } else {
       LMVD_LAUNCH(c, KC_FFT_X_INV, xfl, xby, (k_fft_x_inv<C, 6>), gx, threads(c.fx), smem_bytes(c.fx), c.fx, g, T,
-                  tstride, fo);
+                  tstride, fo, c.dflags);
     }
   }
 }
@@ -1070,8 +1101,8 @@ extern "C" int lmvd_inverse_transform_noalloc(int nx, int ny, int nz, const void
     else k_fft_z_inv<cd, 6, 4><<<gz, threads(fz), smem_bytes(fz), st>>>(fz, g, maps, T, 0, nullptr);
     if (cudaGetLastError() != cudaSuccess) return LMVD_ERR_CUDA;
     dim3 gx(cdiv(cdiv(g.pz, 2), fx.batch), ny, 1);
-    if (fx.ept == 12) k_fft_x_inv<cd, 12><<<gx, threads(fx), smem_bytes(fx), st>>>(fx, g, T, 0, fo);
-    else k_fft_x_inv<cd, 6><<<gx, threads(fx), smem_bytes(fx), st>>>(fx, g, T, 0, fo);
+    if (fx.ept == 12) k_fft_x_inv<cd, 12><<<gx, threads(fx), smem_bytes(fx), st>>>(fx, g, T, 0, fo, nullptr);
+    else k_fft_x_inv<cd, 6><<<gx, threads(fx), smem_bytes(fx), st>>>(fx, g, T, 0, fo, nullptr);
     if (cudaGetLastError() != cudaSuccess) return LMVD_ERR_CUDA;
   }
   return LMVD_OK;
