@@ -268,9 +268,9 @@ template <>
 struct FftMinCtas<cdf> {
   static constexpr int x = 7, z_inv = 3, z_fwd = 4;
 };
-// Loads a thread issues in the x-passes' gather loops before it stores any of them: one load at a time
-// would serialise a memory latency per iteration (ncu: long-scoreboard stalls dominated the double-float
-// passes). The z-passes fetch their tiles with TMA instead (below).
+// Loads a thread issues before it stores any of them, in the forward x-pass's gather and the inverse x-pass's
+// loads of f': one load at a time would serialise a memory latency per iteration (ncu: long-scoreboard
+// stalls dominated the double-float passes). The z-passes and the inverse x-pass's input come by TMA.
 constexpr int FFT_LOAD_CHUNK = 4;
 
 // ---------------------------------------------------------------- tile loads (TMA)
