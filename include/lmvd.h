@@ -187,8 +187,9 @@ size_t lmvd_field_bytes(const lmvd_ctx* ctx, int which);
  * lmvd_inverse_transform: phys(x, z) = sum over retained (kx, kz) of spec exp(i (kx x + kz z)),
  *   the kx < 0 half by Hermitian symmetry (the kx = 0 column is taken as Hermitian).
  * lmvd_forward_transform: spec = retained coefficients of phys, scaled by 1 / ((3nx/2)(3nz/2)).
- * Both pointers must be device memory owned by the caller. Asynchronous.
- * Errors: INVALID_ARG (NULL pointer, nfields < 0), CUDA. */
+ * Both pointers must be device memory owned by the caller; spec of the inverse transform 16-byte aligned
+ * (it is read by TMA tile copies; every complex128 element boundary is). Asynchronous.
+ * Errors: INVALID_ARG (NULL pointer, nfields < 0, spec of the inverse not 16-byte aligned), CUDA. */
 int lmvd_inverse_transform(lmvd_ctx* ctx, const void* spec, double* phys, int nfields);
 int lmvd_forward_transform(lmvd_ctx* ctx, const double* phys, void* spec, int nfields);
 
@@ -210,8 +211,8 @@ int lmvd_forward_transform(lmvd_ctx* ctx, const double* phys, void* spec, int nf
  * Launch errors: a launch error left pending on the calling host thread by earlier, unrelated work is
  * cleared on entry (after the argument checks) and not reported; each of this call's launches is then
  * checked, and the first failure returns CUDA without launching the rest.
- * Errors: INVALID_ARG (NULL pointer, odd or too small nx/nz, ny < 1 or ny > 65535, nfields < 0, grid too
- * large for the static array), UNSUPPORTED (3nx/2 or 3nz/2 with prime factors other than 2 and 3, or
+ * Errors: INVALID_ARG (NULL pointer, spec not 16-byte aligned, odd or too small nx/nz, ny < 1 or
+ * ny > 65535, nfields < 0, grid too large for the static array), UNSUPPORTED (3nx/2 or 3nz/2 with prime factors other than 2 and 3, or
  * above the limits of lmvd_create), CUDA. */
 int lmvd_inverse_transform_noalloc(int nx, int ny, int nz, const void* spec, double* phys, int nfields,
                                    void* cuda_stream);

@@ -1036,7 +1036,8 @@ int lmvd_get_field(lmvd_ctx* h, int which, void* out) {
 }
 
 int lmvd_inverse_transform(lmvd_ctx* h, const void* spec, double* phys, int nfields) {
-  if (!h || !spec || !phys || nfields < 0) return LMVD_ERR_INVALID_ARG;
+  // spec is read by TMA tile copies, which need 16-byte alignment (any complex128 element boundary)
+  if (!h || !spec || !phys || nfields < 0 || ((uintptr_t)spec & 15)) return LMVD_ERR_INVALID_ARG;
   Ctx& c = h->c;
   const size_t S = (size_t)c.g.ny * c.g.M, P = (size_t)c.g.ny * c.g.P;
   for (int f0 = 0; f0 < nfields; f0 += 10) {

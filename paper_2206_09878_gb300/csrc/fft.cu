@@ -1050,7 +1050,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 extern "C" int lmvd_inverse_transform_noalloc(int nx, int ny, int nz, const void* spec, double* phys, int nfields,
                                               void* cuda_stream) {
   using namespace lmvd;
-  if (!spec || !phys || nfields < 0 || ny < 1 || nx < 4 || nz < 4 || (nx % 2) || (nz % 2))
+  if (!spec || !phys || nfields < 0 || ny < 1 || nx < 4 || nz < 4 || (nx % 2) || (nz % 2) || ((uintptr_t)spec & 15))
     return LMVD_ERR_INVALID_ARG;
   if (ny > 65535) return LMVD_ERR_INVALID_ARG;  // ny is the grid's y-dimension (at most 65535 CTAs)
   Grid g{};

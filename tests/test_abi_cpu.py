@@ -105,6 +105,7 @@ def test_host_side_argument_checks_without_gpu(lib):
     assert L.lmvd_inverse_transform_noalloc(2, 9, 8, fake, fake, 1, None) == -1       # nx < 4
     assert L.lmvd_inverse_transform_noalloc(9, 9, 8, fake, fake, 1, None) == -1       # odd nx
     assert L.lmvd_inverse_transform_noalloc(8, 9, 8, None, fake, 1, None) == -1       # NULL spec
+    assert L.lmvd_inverse_transform_noalloc(8, 9, 8, ctypes.c_void_p(24), fake, 1, None) == -1  # spec unaligned
     assert L.lmvd_inverse_transform_noalloc(8, 9, 8, fake, fake, -1, None) == -1      # nfields < 0
     assert L.lmvd_inverse_transform_noalloc(10, 9, 8, fake, fake, 1, None) == -5      # 3nx/2 = 15 = 3 * 5
     assert L.lmvd_inverse_transform_noalloc(4, 70000, 4, fake, fake, 1, None) == -1   # ny > 65535 (fits the array)
