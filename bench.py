@@ -40,13 +40,13 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 DF64_EQ_PEAK_TFLOPS = 152 * 128 * 2.07e9 / 10 / 1e12
 # Measured DRAM bytes (read + write) of the dominant kernel class over its algorithmic bytes, from one ncu
 # capture of a smaller case with the same transform length (512 x 33 x 512: 768-point x-transforms), keyed by
-# (precision, kernel class, transform length). The class fft_x_inverse holds k_fft_x_inv (18936-19329 /
-# 18834-19265 B per complex x-transform against 20480 algorithmic) and k_fft_x_inv_mul, whose epilogue also
-# reads f' (29734-29970 / 29496-29739 B against 32768); over the 12 launches of one substage the measured
+# (precision, kernel class, transform length). The class fft_x_inverse holds k_fft_x_inv (19042-19412 /
+# 18826-19246 B per complex x-transform against 20480 algorithmic) and k_fft_x_inv_mul, whose epilogue also
+# reads f' (30032-30297 / 29464-29716 B against 32768); over the 12 launches of one substage the measured
 # bytes are these fractions of the
 # algorithmic ones (profiles/fft_x_inverse_rt512y33_traffic.md). Full launches: the fraction times the
 # launch's algorithmic bytes.
-NCU_DRAM_FRACTION = {(0, "fft_x_inverse", 768): 0.9257, (1, "fft_x_inverse", 768): 0.9204}
+NCU_DRAM_FRACTION = {(0, "fft_x_inverse", 768): 0.9318, (1, "fft_x_inverse", 768): 0.9199}
 CPU_SAMPLE_N = 128
 
 
